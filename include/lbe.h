@@ -1,0 +1,202 @@
+/*
+ * lbe.h -- C ABI of the GB300 (sm_103a) stabilized Lattice Boltzmann-Enskog
+ * hot path: the per-time-step two-distribution trapezoidal (DD-TR) update of a
+ * hard-sphere fluid or mixture on a D3Q19 lattice.
+ *
+ * Method: S. Melchionna and U. Marini Bettolo Marconi, "Stabilized Lattice
+ * Boltzmann-Enskog method for compressible flows and its application to one
+ * and two-component fluids in nanochannels" (arXiv:1202.3842).  Section and
+ * equation names below refer to that paper.
+ *
+ * Conventions (all functions):
+ *   - Every function returns lbe_status; no C++ exception crosses the ABI and
+ *     nothing aborts.  lbe_last_error() gives a text for the last failure on a
+ *     context (thread-local copy, valid until the next call on that thread).
+ *   - Lattice units: time step h = 1, spacing 1, mass 1, k_B T = v_T^2 = 1/3.
+ *   - Scalar fields are flat arrays of N = nx*ny*nz values, x fastest:
+ *     i = x + nx*(y + ny*z).  Vector fields are [3][N] (component-major).
+ *     Population arrays are [19][N] in the D3Q19 order: rest; +x,-x,+y,-y,+z,-z;
+ *     (+1,+1,0),(-1,-1,0),(+1,-1,0),(-1,+1,0),(+1,0,+1),(-1,0,-1),(+1,0,-1),
+ *     (-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ *   - Host arrays passed in are caller-owned, read during the call and not
+ *     retained.  Host arrays passed out are caller-allocated and filled.
+ *     All host floating-point data is double precision, whatever the storage
+ *     precision on the device.
+ *   - The context owns its device memory (through the allocator given at
+ *     creation) and issues all work on the CUDA stream given at creation.
+ *     lbe_step only enqueues work; getters synchronise that stream.
+ *   - The CUDA kernels are the only compute path: there is no CPU fallback.
+ *     Without a usable sm_103a device lbe_create returns LBE_ERR_CUDA.
+ */
+#ifndef LBE_H
+#define LBE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbe_ctx lbe_ctx;
+
+typedef enum {
+    LBE_OK = 0,
+    LBE_ERR_INVALID_ARG = 1, /* bad pointer, index, size or parameter value */
+    LBE_ERR_UNSUPPORTED = 2, /* valid request this build does not implement  */
+    LBE_ERR_OOM = 3,         /* device allocation failed                     */
+    LBE_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed            */
+    LBE_ERR_DIVERGED = 5,    /* device check found n < 0, a non-finite value,
+                                or a packing xi3 >= 1                        */
+    LBE_ERR_TIMEOUT = 6,     /* reserved: no call in this library waits      */
+    LBE_ERR_STATE = 7        /* call out of order (e.g. step before species) */
+} lbe_status;
+
+/* Storage precision of the populations.  FP64 and FP32 compute in the same
+ * precision; the shifted 16-bit forms store s_p = (f_p - w_p n0)/(w_p n0) and
+ * compute in FP32.  Mass, momentum and flux accumulators are FP64 always. */
+typedef enum {
+    LBE_FP64 = 0,
+    LBE_FP32 = 1,
+    LBE_BF16_SHIFTED = 2,
+    LBE_FP16_SHIFTED = 3
+} lbe_precision;
+
+/* Collision scheme (Sec. "Results": single/double distribution, Euler or
+ * trapezoidal).  Only LBE_DD_TR is implemented. */
+typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_scheme;
+
+/* Optional device allocator.  alloc returns device memory of at least `bytes`
+ * usable on `stream` (NULL on failure); free releases it.  NULL allocator:
+ * the library uses cudaMallocAsync/cudaFreeAsync on the context stream. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} lbe_allocator;
+
+typedef struct {
+    int nx, ny, nz;           /* lattice size, each >= 1                         */
+    int periodic[3];          /* 1 = periodic axis; 0 = closed (outside = wall)  */
+    int nspecies;             /* M, 1..4                                         */
+    lbe_precision precision;
+    lbe_scheme scheme;        /* LBE_DD_TR                                       */
+    int enable_visc;          /* C^{alpha,visc} (Appendix): must be 0             */
+    int consistent_moments;   /* 0 (default): moments as printed in Sec. "Hard
+                                 sphere fluid mixture": J = J~ + (C^mf + nF)/2,
+                                 Pi = Pi~ - C^mf.u^alpha/2.  1: the map
+                                 g = g~ + Omega/2 applied to the printed S_g:
+                                 J = J~ + nF/2, Pi = Pi~ + beta C^mf.u^alpha/2. */
+    int check_every;          /* > 0: lbe_step checks the device error word every
+                                 this many steps (one stream sync each); 0: only
+                                 getters check                                   */
+} lbe_config;
+
+/* Create a context.  cfg is copied.  cuda_stream is a cudaStream_t (NULL = the
+ * legacy default stream).  The current CUDA device at this call is the
+ * device used for every later call.  *out receives the context. */
+lbe_status lbe_create(const lbe_config *cfg, const lbe_allocator *allocator, void *cuda_stream, lbe_ctx **out);
+
+/* Release all device memory of the context (after synchronising its stream). */
+void lbe_destroy(lbe_ctx *ctx);
+
+/* Solid mask (Sec. "Channel flow with a bottleneck": no-slip walls by mid-point
+ * bounce-back of f and g).  solid[N]: nonzero = solid node.  Solid nodes carry
+ * no fluid: their density is 0 and links into them bounce back. */
+lbe_status lbe_set_geometry(lbe_ctx *ctx, const uint8_t *solid);
+
+/* Species s (0-based): hard-sphere diameter sigma >= 0 in lattice units
+ * (sigma = 0: ideal gas, C^mf = 0), mass (must be 1: the paper's common mass m),
+ * relaxation time tau > 1/2 with omega h = 1/(tau - 1/2), i.e. the TR
+ * relaxation factor omega h/(1 + omega h/2) equals 1/tau (Sec. "Ideal fluid").
+ * The force stencil is tabulated at compile time for integer pair diameters
+ * (sigma_a + sigma_b)/2 in 1..8 and pure ideal gas; other values return
+ * LBE_ERR_UNSUPPORTED. */
+lbe_status lbe_set_species(lbe_ctx *ctx, int s, double sigma, double mass, double tau);
+
+/* External potential V^s[N] (lattice energy units; 1 k_B T = 1/3) of species s.
+ * The force is F = -grad_h V (isotropic D3Q19 gradient; a neighbour outside a
+ * closed axis contributes V(r)); Sec. "Ideal fluid", F = -grad U. */
+lbe_status lbe_set_potential(lbe_ctx *ctx, int s, const double *V);
+
+/* Wall potential a(r) phi(r), added to the potential of every species.
+ * phi[N] is the shape, amp[N] the per-node amplitude (energy units). */
+lbe_status lbe_set_wall_potential(lbe_ctx *ctx, const double *phi, const double *amp);
+
+/* Uniform body force g[3] per unit mass on species s (Sec. "Channel flow"). */
+lbe_status lbe_set_body_force(lbe_ctx *ctx, int s, const double g[3]);
+
+/* Populations at rest: f~_p = g~_p = w_p n[i] on fluid nodes, 0 on solid nodes
+ * (so Pi(0) = n(0)).  n[N] >= 0.  Also sets the reference density n0 of the
+ * shifted 16-bit storage to the fluid-node mean of n, resets the step counter
+ * and the flux average. */
+lbe_status lbe_init_density(lbe_ctx *ctx, int s, const double *n);
+
+/* Advance nsteps >= 0 DD-TR steps (Sec. "Hard sphere fluid mixture in a
+ * potential well": moments, f_eq, g_eq, S_f, S_g, trapezoidal collision,
+ * streaming).  Enqueues work and returns; see check_every. */
+lbe_status lbe_step(lbe_ctx *ctx, int nsteps);
+
+/* Density n^s of the current state, out[N] (synchronises). */
+lbe_status lbe_get_density(lbe_ctx *ctx, int s, double *out);
+
+/* Velocity of the current state, out[3][N]: u^s = J^s/n^s for s >= 0, the
+ * barycentric u = sum J / sum n for s = -1; 0 where the density is 0. */
+lbe_status lbe_get_velocity(lbe_ctx *ctx, int s, double *out);
+
+/* Momentum density J^s of the current state, out[3][N]. */
+lbe_status lbe_get_momentum(lbe_ctx *ctx, int s, double *out);
+
+/* Mean-field Enskog force C^{s,mf} of the current state, out[3][N]
+ * (Appendix, hard-sphere C^{alpha,mf}). */
+lbe_status lbe_get_force(lbe_ctx *ctx, int s, double *out);
+
+/* Contact values g_ab of the current state, out[N], for species pair (a, b). */
+lbe_status lbe_get_contact(lbe_ctx *ctx, int a, int b, double *out);
+
+/* Choose the plane whose flux is accumulated every step: axis 0/1/2, plane
+ * index along that axis.  Resets the time average.  plane < 0 disables. */
+lbe_status lbe_set_flux_plane(lbe_ctx *ctx, int axis, int plane);
+
+/* Flux through the configured plane: *instantaneous = sum over the plane's
+ * fluid nodes of J^s_axis for the last step taken (s = -1: all species);
+ * *time_avg = mean over the steps since the plane was set or reset.  Either
+ * pointer may be NULL. */
+lbe_status lbe_get_flux(lbe_ctx *ctx, int s, double *instantaneous, double *time_avg);
+
+/* Restart the flux time average. */
+lbe_status lbe_reset_flux_average(lbe_ctx *ctx);
+
+/* Totals of the current state: mass[M] = sum n^s, momentum[3] = sum_s sum J^s,
+ * *max_u = max over fluid nodes of |u| (barycentric).  FP64 accumulation.
+ * Any pointer may be NULL. */
+lbe_status lbe_get_totals(lbe_ctx *ctx, double *mass, double *momentum, double *max_u);
+
+/* Streamed populations f~(r,t), g~(r,t) of species s as [19][N] doubles (read
+ * or overwrite the state).  Setting them also resets the flux average. */
+lbe_status lbe_get_populations(lbe_ctx *ctx, int s, double *f, double *g);
+lbe_status lbe_set_populations(lbe_ctx *ctx, int s, const double *f, const double *g);
+
+/* Number of steps taken since lbe_init_density / lbe_set_populations. */
+lbe_status lbe_get_step_count(lbe_ctx *ctx, long long *steps);
+
+/* Per-node blocked-link mask (bit p set: the population arriving along c_p
+ * comes from a solid node or from outside a closed axis), out[N]. */
+lbe_status lbe_get_link_mask(lbe_ctx *ctx, uint32_t *out);
+
+/* Contact shell of diameter sigma used by the force kernels (integer lattice
+ * vectors e with sigma - 1/2 <= |e| < sigma + 1/2).  Writes up to cap vectors
+ * as [k][3] ints into e (may be NULL) and the count into *count. */
+lbe_status lbe_shell(double sigma, int *e, int cap, int *count);
+
+/* Number of kernel launches this context has issued (all entry points). */
+lbe_status lbe_get_launch_count(lbe_ctx *ctx, long long *launches);
+
+const char *lbe_status_string(lbe_status status);
+const char *lbe_last_error(lbe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBE_H */

@@ -1,0 +1,850 @@
+// C ABI of the Lattice Boltzmann-Enskog library (include/lbe.h): context,
+// device memory, set-up, the time-step driver and the getters.  All compute
+// runs in the kernels of lbe_kernels.cu and lbe_shell.cu on the context stream.
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbe.h"
+#include "lbe_device.cuh"
+#include "lbe_launch.h"
+#include "lbe_shell.cuh"
+
+using namespace lbe;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PairShell {
+    int a, b, S;
+    double coef;  // -kT sigma_ab^2 w_ab
+    CUtensorMap map_n, map_gn;
+};
+
+}  // namespace
+
+struct lbe_ctx {
+    lbe_config cfg{};
+    Prec prec = Prec::F32;
+    Grid g{};
+    int M = 1;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    lbe_allocator alloc{};
+    bool have_alloc = false;
+
+    // species
+    double sigma[MAXS] = {0}, tau[MAXS] = {0}, gbody[MAXS][3] = {{0}};
+    bool species_set[MAXS] = {false};
+    double n0[MAXS] = {0};
+
+    // host copies
+    std::vector<uint8_t> solid_h;
+
+    // device buffers
+    Buf pop[2];
+    int cur = 0;
+    Buf solid, mask, V, phi, amp, F;
+    Buf npad, gab, gnpad, C, ball;
+    Buf flux_buf, flux_acc, flux_last;
+    Buf err;
+    Buf scratch64;  // FP64 scratch for getters: n [M][N] + J [M][3][N] (+ more)
+    Buf partial, red_out;
+
+    // derived state
+    bool geom_dirty = true, force_dirty = true, fields_dirty = true;
+    std::vector<PairShell> pairs;
+    ContactParams cparams{};
+    int H = 0;
+
+    long long steps = 0;
+    long long flux_count = 0;
+    int flux_axis = -1, flux_plane = -1;
+    long long launches = 0;
+    long long steps_since_check = 0;
+    std::string last_error;
+};
+
+namespace {
+
+lbe_status fail(lbe_ctx *c, lbe_status s, const std::string &msg) {
+    t_last_error = msg;
+    if (c) c->last_error = msg;
+    return s;
+}
+
+lbe_status cuda_fail(lbe_ctx *c, cudaError_t e, const char *where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, LBE_ERR_CUDA, m);
+}
+
+#define CK(call, where)                                  \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+    } while (0)
+
+#define LAUNCH(call, where)                              \
+    do {                                                 \
+        cudaError_t _e = (call);                         \
+        c->launches += 1;                                \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, where); \
+    } while (0)
+
+lbe_status dev_alloc(lbe_ctx *c, Buf &b, size_t bytes) {
+    if (b.p && b.bytes >= bytes) return LBE_OK;
+    if (b.p) {
+        if (c->have_alloc)
+            c->alloc.free(b.p, b.bytes, c->stream, c->alloc.user);
+        else
+            cudaFreeAsync(b.p, c->stream);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) / 256 * 256;
+    void *p = nullptr;
+    if (c->have_alloc) {
+        p = c->alloc.alloc(bytes, c->stream, c->alloc.user);
+        if (!p) return fail(c, LBE_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, c->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, LBE_ERR_OOM, std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return LBE_OK;
+}
+
+void dev_free(lbe_ctx *c, Buf &b) {
+    if (!b.p) return;
+    if (c->have_alloc)
+        c->alloc.free(b.p, b.bytes, c->stream, c->alloc.user);
+    else
+        cudaFreeAsync(b.p, c->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+#define TRY(x)                          \
+    do {                                \
+        lbe_status _s = (x);            \
+        if (_s != LBE_OK) return _s;    \
+    } while (0)
+
+size_t real_bytes(const lbe_ctx *c) { return prec_fp64(c->prec) ? 8 : 4; }
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+lbe_status make_map(lbe_ctx *c, CUtensorMap *map, void *base, int S) {
+    auto enc = get_encode();
+    if (!enc) return fail(c, LBE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const bool f64 = prec_fp64(c->prec);
+    int bx = 0, by = 0;
+    shell_box(f64, S, &bx, &by);
+    const size_t es = f64 ? 8 : 4;
+    cuuint64_t dims[3] = {(cuuint64_t)c->g.px, (cuuint64_t)c->g.py, (cuuint64_t)c->g.pz};
+    cuuint64_t strides[2] = {(cuuint64_t)c->g.px * es, (cuuint64_t)c->g.px * c->g.py * es};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, LBE_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return LBE_OK;
+}
+
+const double kPi = 3.14159265358979323846;
+const double kKT = 1.0 / 3.0;
+
+// Shell weight w_sigma = 4 pi sigma / sum_{e in K_sigma} |e| (so that a linear
+// density reproduces the continuum k^ integral).
+double shell_weight(int S) {
+    double sum = 0.0;
+    for (int z = -S; z <= S; ++z)
+        for (int y = -S; y <= S; ++y)
+            for (int x = -S; x <= S; ++x)
+                if (in_shell(S, x, y, z)) sum += std::sqrt((double)(x * x + y * y + z * z));
+    return 4.0 * kPi * S / sum;
+}
+
+bool integer_diameter(double s, int *S) {
+    double r = std::nearbyint(s);
+    if (std::fabs(s - r) > 1e-12) return false;
+    *S = (int)r;
+    return true;
+}
+
+// Set up everything that depends on the species, geometry and potentials:
+// halo width, padded fields, tensor maps, ball tables, force field.
+lbe_status prepare(lbe_ctx *c) {
+    for (int a = 0; a < c->M; ++a)
+        if (!c->species_set[a]) return fail(c, LBE_ERR_STATE, "species " + std::to_string(a) + " not set");
+    const bool f64 = prec_fp64(c->prec);
+    if (c->fields_dirty) {
+        // pair shells
+        c->pairs.clear();
+        int H = 1;
+        for (int a = 0; a < c->M; ++a)
+            for (int b = 0; b < c->M; ++b) {
+                double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
+                if (!(sab > 0.0)) continue;
+                int S = 0;
+                if (!integer_diameter(sab, &S) || !shell_supported(f64, S))
+                    return fail(c, LBE_ERR_UNSUPPORTED,
+                                "pair diameter " + std::to_string(sab) + " has no compiled shell stencil");
+                PairShell ps{};
+                ps.a = a;
+                ps.b = b;
+                ps.S = S;
+                ps.coef = -kKT * sab * sab * shell_weight(S);
+                c->pairs.push_back(ps);
+                H = std::max(H, S);
+            }
+        // ball radii
+        std::vector<int> ball;
+        ContactParams cp{};
+        cp.M = c->M;
+        for (int b = 0; b < c->M; ++b) {
+            double R = 0.5 * c->sigma[b];
+            int Ri = (int)std::floor(R);
+            H = std::max(H, Ri);
+            cp.sigma[b] = c->sigma[b];
+            cp.xi2c[b] = kPi / 6.0 * c->sigma[b] * c->sigma[b];
+            cp.xi3c[b] = kPi / 6.0 * c->sigma[b] * c->sigma[b] * c->sigma[b];
+        }
+        c->H = H;
+        Grid &g = c->g;
+        g.H = H;
+        g.px = (g.nx + 2 * H + 7) / 8 * 8;
+        g.py = g.ny + 2 * H;
+        g.pz = g.nz + 2 * H;
+        g.P = (long long)g.px * g.py * g.pz;
+        for (int b = 0; b < c->M; ++b) {
+            double R = 0.5 * c->sigma[b];
+            int Ri = (int)std::floor(R);
+            cp.ball_start[b] = (int)ball.size();
+            for (int z = -Ri; z <= Ri; ++z)
+                for (int y = -Ri; y <= Ri; ++y)
+                    for (int x = -Ri; x <= Ri; ++x)
+                        if ((double)(x * x + y * y + z * z) <= R * R)
+                            ball.push_back(x + g.px * (y + g.py * z));
+            cp.ball_count[b] = (int)ball.size() - cp.ball_start[b];
+        }
+        for (int a = 0; a < c->M; ++a)
+            for (int b = 0; b < c->M; ++b) {
+                double sa = c->sigma[a], sb = c->sigma[b];
+                cp.s_ab[a][b] = (sa + sb > 0.0) ? sa * sb / (sa + sb) : 0.0;
+            }
+        c->cparams = cp;
+        const size_t rb = real_bytes(c);
+        TRY(dev_alloc(c, c->npad, rb * c->M * g.P));
+        TRY(dev_alloc(c, c->gnpad, rb * c->M * c->M * g.P));
+        TRY(dev_alloc(c, c->gab, rb * c->M * c->M * g.N));
+        TRY(dev_alloc(c, c->C, rb * c->M * 3 * g.N));
+        TRY(dev_alloc(c, c->ball, sizeof(int) * ball.size()));
+        CK(cudaMemsetAsync(c->npad.p, 0, rb * c->M * g.P, c->stream), "memset npad");
+        CK(cudaMemsetAsync(c->gnpad.p, 0, rb * c->M * c->M * g.P, c->stream), "memset gnpad");
+        CK(cudaMemsetAsync(c->C.p, 0, rb * c->M * 3 * g.N, c->stream), "memset C");
+        CK(cudaMemcpyAsync(c->ball.p, ball.data(), sizeof(int) * ball.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy ball table");
+        for (auto &ps : c->pairs) {
+            char *nb = (char *)c->npad.p + rb * ps.b * g.P;
+            char *gn = (char *)c->gnpad.p + rb * (ps.a * c->M + ps.b) * g.P;
+            TRY(make_map(c, &ps.map_n, nb, ps.S));
+            TRY(make_map(c, &ps.map_gn, gn, ps.S));
+        }
+        c->fields_dirty = false;
+    }
+    if (c->force_dirty) {
+        const size_t rb = real_bytes(c);
+        TRY(dev_alloc(c, c->F, rb * c->M * 3 * c->g.N));
+        for (int a = 0; a < c->M; ++a) {
+            LAUNCH(launch_force_field(c->prec, c->g, (const double *)c->V.p + (long long)a * c->g.N,
+                                      (const double *)c->phi.p, (const double *)c->amp.p, c->gbody[a],
+                                      (char *)c->F.p + rb * 3 * a * c->g.N, c->stream),
+                   "force field");
+        }
+        c->force_dirty = false;
+    }
+    return LBE_OK;
+}
+
+StepParams step_params(const lbe_ctx *c) {
+    StepParams sp{};
+    sp.M = c->M;
+    sp.consistent = c->cfg.consistent_moments ? 1 : 0;
+    sp.flux_axis = c->flux_plane >= 0 ? c->flux_axis : -1;
+    sp.flux_plane = c->flux_plane;
+    for (int a = 0; a < c->M; ++a) {
+        double omega = 1.0 / (c->tau[a] - 0.5);
+        sp.sp[a].omega_eff = omega / (1.0 + 0.5 * omega);
+        sp.sp[a].inv = 1.0 / (1.0 + 0.5 * omega);
+        sp.sp[a].n0 = c->n0[a];
+    }
+    return sp;
+}
+
+// K1 -> K2 -> K3 for the current populations (fills npad, gab, gnpad, C).
+lbe_status force_stage(lbe_ctx *c) {
+    const bool f64 = prec_fp64(c->prec);
+    const size_t rb = real_bytes(c);
+    LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->M, c->n0, c->npad.p,
+                          (int *)c->err.p, c->stream),
+           "density kernel");
+    if (c->pairs.empty()) return LBE_OK;  // ideal gas: C stays zero
+    LAUNCH(launch_contact(f64, c->g, c->cparams, (const int *)c->ball.p, c->npad.p, c->gab.p, c->gnpad.p,
+                          (int *)c->err.p, c->stream),
+           "contact kernel");
+    std::vector<int> first(c->M, 1);
+    for (auto &ps : c->pairs) {
+        ShellLaunch L{};
+        L.grid = &c->g;
+        L.map_n = &ps.map_n;
+        L.map_gn = &ps.map_gn;
+        L.npad_a = (const char *)c->npad.p + rb * ps.a * c->g.P;
+        L.g_ab = (const char *)c->gab.p + rb * (ps.a * c->M + ps.b) * c->g.N;
+        L.Cout = (char *)c->C.p + rb * 3 * ps.a * c->g.N;
+        L.coef = ps.coef;
+        L.accumulate = first[ps.a] ? 0 : 1;
+        L.err = (int *)c->err.p;
+        first[ps.a] = 0;
+        LAUNCH(launch_shell_force(f64, ps.S, L, c->stream), "shell force kernel");
+    }
+    for (int a = 0; a < c->M; ++a)
+        if (first[a]) CK(cudaMemsetAsync((char *)c->C.p + rb * 3 * a * c->g.N, 0, rb * 3 * c->g.N, c->stream),
+                         "memset C");
+    return LBE_OK;
+}
+
+int plane_size(const lbe_ctx *c) {
+    const Grid &g = c->g;
+    return c->flux_axis == 0 ? g.ny * g.nz : (c->flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
+}
+
+lbe_status check_error_word(lbe_ctx *c) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error word");
+    CK(cudaStreamSynchronize(c->stream), "stream sync");
+    if (e & ERR_TMA_WAIT) return fail(c, LBE_ERR_CUDA, "a TMA wait in the shell kernel gave up");
+    if (e & ERR_DENSITY) return fail(c, LBE_ERR_DIVERGED, "negative or non-finite density");
+    if (e & ERR_PACKING) return fail(c, LBE_ERR_DIVERGED, "local packing xi3 >= 1 or non-finite contact value");
+    return LBE_OK;
+}
+
+lbe_status ready(lbe_ctx *c) {
+    if (!c) return fail(nullptr, LBE_ERR_INVALID_ARG, "null context");
+    CK(cudaSetDevice(c->device), "cudaSetDevice");
+    return LBE_OK;
+}
+
+// n [M][N] and J [M][3][N] (FP64, device scratch) of the current state.
+lbe_status state_moments(lbe_ctx *c, double **n, double **J) {
+    TRY(prepare(c));
+    TRY(force_stage(c));
+    const long long N = c->g.N;
+    TRY(dev_alloc(c, c->scratch64, sizeof(double) * ((size_t)c->M * 4 * N + 4 * N)));
+    *n = (double *)c->scratch64.p;
+    *J = *n + (long long)c->M * N;
+    StepParams sp = step_params(c);
+    LAUNCH(launch_moments(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, *n, *J,
+                          c->stream),
+           "moments kernel");
+    return LBE_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *lbe_status_string(lbe_status s) {
+    switch (s) {
+        case LBE_OK: return "ok";
+        case LBE_ERR_INVALID_ARG: return "invalid argument";
+        case LBE_ERR_UNSUPPORTED: return "unsupported";
+        case LBE_ERR_OOM: return "out of device memory";
+        case LBE_ERR_CUDA: return "CUDA error";
+        case LBE_ERR_DIVERGED: return "diverged";
+        case LBE_ERR_TIMEOUT: return "timeout";
+        case LBE_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char *lbe_last_error(lbe_ctx *ctx) {
+    (void)ctx;
+    return t_last_error.c_str();
+}
+
+lbe_status lbe_create(const lbe_config *cfg, const lbe_allocator *allocator, void *cuda_stream, lbe_ctx **out) {
+    lbe_ctx *c = nullptr;
+    if (!cfg || !out) return fail(nullptr, LBE_ERR_INVALID_ARG, "null config or output pointer");
+    *out = nullptr;
+    if (cfg->nx < 1 || cfg->ny < 1 || cfg->nz < 1) return fail(nullptr, LBE_ERR_INVALID_ARG, "lattice sizes must be >= 1");
+    if ((long long)cfg->nx * cfg->ny * cfg->nz > (1ll << 31) - 1)
+        return fail(nullptr, LBE_ERR_INVALID_ARG, "lattice larger than 2^31 - 1 nodes");
+    if (cfg->nspecies < 1 || cfg->nspecies > MAXS) return fail(nullptr, LBE_ERR_INVALID_ARG, "nspecies must be 1..4");
+    if (cfg->precision < LBE_FP64 || cfg->precision > LBE_FP16_SHIFTED)
+        return fail(nullptr, LBE_ERR_INVALID_ARG, "unknown precision");
+    if (cfg->scheme != LBE_DD_TR) return fail(nullptr, LBE_ERR_UNSUPPORTED, "only the DD-TR scheme is implemented");
+    if (cfg->enable_visc) return fail(nullptr, LBE_ERR_UNSUPPORTED, "the viscous Enskog force is not implemented");
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(nullptr, LBE_ERR_INVALID_ARG, "allocator needs both alloc and free");
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(nullptr, LBE_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return fail(nullptr, LBE_ERR_CUDA, std::string("cudaGetDeviceProperties: ") + cudaGetErrorString(e));
+    if (!(prop.major == 10 && prop.minor == 3))
+        return fail(nullptr, LBE_ERR_CUDA,
+                    "this library is built for sm_103a only; device is sm_" + std::to_string(prop.major) +
+                        std::to_string(prop.minor));
+
+    c = new (std::nothrow) lbe_ctx();
+    if (!c) return fail(nullptr, LBE_ERR_OOM, "host allocation failed");
+    c->cfg = *cfg;
+    c->prec = (Prec)cfg->precision;
+    c->device = dev;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (allocator) {
+        c->alloc = *allocator;
+        c->have_alloc = true;
+    }
+    c->M = cfg->nspecies;
+    Grid &g = c->g;
+    g.nx = cfg->nx;
+    g.ny = cfg->ny;
+    g.nz = cfg->nz;
+    for (int k = 0; k < 3; ++k) g.per[k] = cfg->periodic[k] ? 1 : 0;
+    g.N = (long long)g.nx * g.ny * g.nz;
+    for (int a = 0; a < MAXS; ++a) c->tau[a] = 1.0;
+
+    const size_t pb = (size_t)prec_bytes(c->prec) * c->M * 2 * Q * g.N;
+    lbe_status s;
+    if ((s = dev_alloc(c, c->pop[0], pb)) != LBE_OK || (s = dev_alloc(c, c->pop[1], pb)) != LBE_OK ||
+        (s = dev_alloc(c, c->solid, g.N)) != LBE_OK || (s = dev_alloc(c, c->mask, 4 * g.N)) != LBE_OK ||
+        (s = dev_alloc(c, c->V, 8 * c->M * g.N)) != LBE_OK || (s = dev_alloc(c, c->phi, 8 * g.N)) != LBE_OK ||
+        (s = dev_alloc(c, c->amp, 8 * g.N)) != LBE_OK || (s = dev_alloc(c, c->err, 64)) != LBE_OK ||
+        (s = dev_alloc(c, c->flux_acc, 8 * MAXS)) != LBE_OK || (s = dev_alloc(c, c->flux_last, 8 * MAXS)) != LBE_OK ||
+        (s = dev_alloc(c, c->partial, 16 * 1024)) != LBE_OK || (s = dev_alloc(c, c->red_out, 64)) != LBE_OK) {
+        lbe_destroy(c);
+        return s;
+    }
+    cudaMemsetAsync(c->pop[0].p, 0, pb, c->stream);
+    cudaMemsetAsync(c->pop[1].p, 0, pb, c->stream);
+    cudaMemsetAsync(c->solid.p, 0, g.N, c->stream);
+    cudaMemsetAsync(c->V.p, 0, 8 * c->M * g.N, c->stream);
+    cudaMemsetAsync(c->phi.p, 0, 8 * g.N, c->stream);
+    cudaMemsetAsync(c->amp.p, 0, 8 * g.N, c->stream);
+    cudaMemsetAsync(c->err.p, 0, 64, c->stream);
+    cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream);
+    cudaMemsetAsync(c->flux_last.p, 0, 8 * MAXS, c->stream);
+    c->solid_h.assign(g.N, 0);
+    e = launch_link_mask(g, (const uint8_t *)c->solid.p, (uint32_t *)c->mask.p, c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        cuda_fail(c, e, "create");
+        lbe_destroy(c);
+        return LBE_ERR_CUDA;
+    }
+    *out = c;
+    return LBE_OK;
+}
+
+void lbe_destroy(lbe_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
+                  &c->npad, &c->gab, &c->gnpad, &c->C, &c->ball, &c->flux_buf, &c->flux_acc,
+                  &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out};
+    for (Buf *b : all) dev_free(c, *b);
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+lbe_status lbe_set_geometry(lbe_ctx *c, const uint8_t *solid) {
+    TRY(ready(c));
+    if (!solid) return fail(c, LBE_ERR_INVALID_ARG, "null solid mask");
+    const long long N = c->g.N;
+    for (long long i = 0; i < N; ++i) c->solid_h[i] = solid[i] ? 1 : 0;
+    CK(cudaMemcpyAsync(c->solid.p, c->solid_h.data(), N, cudaMemcpyHostToDevice, c->stream), "copy solid");
+    LAUNCH(launch_link_mask(c->g, (const uint8_t *)c->solid.p, (uint32_t *)c->mask.p, c->stream), "link mask");
+    CK(cudaStreamSynchronize(c->stream), "stream sync");
+    return LBE_OK;
+}
+
+lbe_status lbe_set_species(lbe_ctx *c, int s, double sigma, double mass, double tau) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M) return fail(c, LBE_ERR_INVALID_ARG, "species index out of range");
+    if (!(sigma >= 0.0) || !std::isfinite(sigma)) return fail(c, LBE_ERR_INVALID_ARG, "sigma must be >= 0");
+    if (mass != 1.0) return fail(c, LBE_ERR_UNSUPPORTED, "species share the common mass m = 1");
+    if (!(tau > 0.5) || !std::isfinite(tau)) return fail(c, LBE_ERR_INVALID_ARG, "tau must be > 1/2");
+    if (sigma > 16.0) return fail(c, LBE_ERR_UNSUPPORTED, "sigma above 16 lattice units");
+    c->sigma[s] = sigma;
+    c->tau[s] = tau;
+    c->species_set[s] = true;
+    c->fields_dirty = true;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_potential(lbe_ctx *c, int s, const double *V) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !V) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null potential");
+    CK(cudaMemcpyAsync((double *)c->V.p + (long long)s * c->g.N, V, 8 * c->g.N, cudaMemcpyHostToDevice, c->stream),
+       "copy potential");
+    CK(cudaStreamSynchronize(c->stream), "stream sync");
+    c->force_dirty = true;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_wall_potential(lbe_ctx *c, const double *phi, const double *amp) {
+    TRY(ready(c));
+    if (!phi || !amp) return fail(c, LBE_ERR_INVALID_ARG, "null wall potential array");
+    CK(cudaMemcpyAsync(c->phi.p, phi, 8 * c->g.N, cudaMemcpyHostToDevice, c->stream), "copy phi");
+    CK(cudaMemcpyAsync(c->amp.p, amp, 8 * c->g.N, cudaMemcpyHostToDevice, c->stream), "copy amp");
+    CK(cudaStreamSynchronize(c->stream), "stream sync");
+    c->force_dirty = true;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_body_force(lbe_ctx *c, int s, const double gb[3]) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !gb) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null force");
+    for (int k = 0; k < 3; ++k) c->gbody[s][k] = gb[k];
+    c->force_dirty = true;
+    return LBE_OK;
+}
+
+static void reset_counters(lbe_ctx *c) {
+    c->steps = 0;
+    c->flux_count = 0;
+    cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream);
+    cudaMemsetAsync(c->flux_last.p, 0, 8 * MAXS, c->stream);
+}
+
+lbe_status lbe_init_density(lbe_ctx *c, int s, const double *n) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !n) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null density");
+    const long long N = c->g.N;
+    double sum = 0.0;
+    long long cnt = 0;
+    for (long long i = 0; i < N; ++i) {
+        if (!(n[i] >= 0.0) || !std::isfinite(n[i])) return fail(c, LBE_ERR_INVALID_ARG, "density must be finite and >= 0");
+        if (!c->solid_h[i]) {
+            sum += n[i];
+            ++cnt;
+        }
+    }
+    c->n0[s] = cnt > 0 ? sum / cnt : 0.0;
+    if (c->prec == Prec::BF16 || c->prec == Prec::F16) {
+        if (!(c->n0[s] > 0.0)) return fail(c, LBE_ERR_INVALID_ARG, "shifted storage needs a positive mean density");
+    }
+    Buf tmp;
+    TRY(dev_alloc(c, tmp, 8 * N));
+    cudaError_t e = cudaMemcpyAsync(tmp.p, n, 8 * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_rest_state(c->prec, c->g, (const uint32_t *)c->mask.p, (const double *)tmp.p, c->pop[c->cur].p, s,
+                              c->n0[s], c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "init density");
+    reset_counters(c);
+    return LBE_OK;
+}
+
+lbe_status lbe_step(lbe_ctx *c, int nsteps) {
+    TRY(ready(c));
+    if (nsteps < 0) return fail(c, LBE_ERR_INVALID_ARG, "nsteps must be >= 0");
+    TRY(prepare(c));
+    StepParams sp = step_params(c);
+    const int psize = c->flux_plane >= 0 ? plane_size(c) : 0;
+    if (psize > 0) TRY(dev_alloc(c, c->flux_buf, 8 * (size_t)c->M * psize));
+    for (int t = 0; t < nsteps; ++t) {
+        TRY(force_stage(c));
+        LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
+                              c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
+               "collide kernel");
+        c->cur = 1 - c->cur;
+        if (psize > 0) {
+            LAUNCH(launch_flux_reduce(c->M, psize, (const double *)c->flux_buf.p, (double *)c->flux_acc.p,
+                                      (double *)c->flux_last.p, c->stream),
+                   "flux reduction");
+            c->flux_count += 1;
+        }
+        c->steps += 1;
+        c->steps_since_check += 1;
+        if (c->cfg.check_every > 0 && c->steps_since_check >= c->cfg.check_every) {
+            c->steps_since_check = 0;
+            TRY(check_error_word(c));
+        }
+    }
+    return LBE_OK;
+}
+
+lbe_status lbe_get_density(lbe_ctx *c, int s, double *out) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    double *n, *J;
+    TRY(state_moments(c, &n, &J));
+    CK(cudaMemcpyAsync(out, n + (long long)s * c->g.N, 8 * c->g.N, cudaMemcpyDeviceToHost, c->stream), "copy density");
+    return check_error_word(c);
+}
+
+lbe_status lbe_get_momentum(lbe_ctx *c, int s, double *out) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    double *n, *J;
+    TRY(state_moments(c, &n, &J));
+    CK(cudaMemcpyAsync(out, J + (long long)s * 3 * c->g.N, 24 * c->g.N, cudaMemcpyDeviceToHost, c->stream),
+       "copy momentum");
+    return check_error_word(c);
+}
+
+lbe_status lbe_get_velocity(lbe_ctx *c, int s, double *out) {
+    TRY(ready(c));
+    if (s < -1 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    const long long N = c->g.N;
+    double *dn, *dJ;
+    TRY(state_moments(c, &dn, &dJ));
+    double *du = dJ + (long long)c->M * 3 * N;  // scratch holds n, J and 4 more fields
+    LAUNCH(launch_velocity(c->M, N, s, dn, dJ, du, nullptr, c->stream), "velocity kernel");
+    CK(cudaMemcpyAsync(out, du, 24 * N, cudaMemcpyDeviceToHost, c->stream), "copy velocity");
+    return check_error_word(c);
+}
+
+lbe_status lbe_get_force(lbe_ctx *c, int s, double *out) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    TRY(prepare(c));
+    TRY(force_stage(c));
+    const long long N = c->g.N;
+    TRY(dev_alloc(c, c->scratch64, sizeof(double) * (size_t)c->M * 4 * N));
+    LAUNCH(launch_to_f64(prec_fp64(c->prec), (const char *)c->C.p + real_bytes(c) * 3 * s * N, 3 * N,
+                         (double *)c->scratch64.p, c->stream),
+           "convert force");
+    CK(cudaMemcpyAsync(out, c->scratch64.p, 24 * N, cudaMemcpyDeviceToHost, c->stream), "copy force");
+    return check_error_word(c);
+}
+
+lbe_status lbe_get_contact(lbe_ctx *c, int a, int b, double *out) {
+    TRY(ready(c));
+    if (a < 0 || a >= c->M || b < 0 || b >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad pair or null output");
+    TRY(prepare(c));
+    TRY(force_stage(c));
+    const long long N = c->g.N;
+    if (c->pairs.empty()) {
+        for (long long i = 0; i < N; ++i) out[i] = 1.0;
+        return check_error_word(c);
+    }
+    TRY(dev_alloc(c, c->scratch64, sizeof(double) * (size_t)c->M * 4 * N));
+    LAUNCH(launch_to_f64(prec_fp64(c->prec), (const char *)c->gab.p + real_bytes(c) * (a * c->M + b) * N, N,
+                         (double *)c->scratch64.p, c->stream),
+           "convert contact");
+    CK(cudaMemcpyAsync(out, c->scratch64.p, 8 * N, cudaMemcpyDeviceToHost, c->stream), "copy contact");
+    return check_error_word(c);
+}
+
+lbe_status lbe_set_flux_plane(lbe_ctx *c, int axis, int plane) {
+    TRY(ready(c));
+    if (axis < 0 || axis > 2) return fail(c, LBE_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+    const int n = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+    if (plane >= n) return fail(c, LBE_ERR_INVALID_ARG, "plane index out of range");
+    c->flux_axis = axis;
+    c->flux_plane = plane < 0 ? -1 : plane;
+    c->flux_count = 0;
+    CK(cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream), "memset flux");
+    CK(cudaMemsetAsync(c->flux_last.p, 0, 8 * MAXS, c->stream), "memset flux");
+    return LBE_OK;
+}
+
+lbe_status lbe_reset_flux_average(lbe_ctx *c) {
+    TRY(ready(c));
+    c->flux_count = 0;
+    CK(cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream), "memset flux");
+    return LBE_OK;
+}
+
+lbe_status lbe_get_flux(lbe_ctx *c, int s, double *inst, double *avg) {
+    TRY(ready(c));
+    if (s < -1 || s >= c->M) return fail(c, LBE_ERR_INVALID_ARG, "bad species index");
+    if (c->flux_plane < 0) return fail(c, LBE_ERR_STATE, "no flux plane set");
+    double acc[MAXS], last[MAXS];
+    CK(cudaMemcpyAsync(acc, c->flux_acc.p, 8 * MAXS, cudaMemcpyDeviceToHost, c->stream), "copy flux");
+    CK(cudaMemcpyAsync(last, c->flux_last.p, 8 * MAXS, cudaMemcpyDeviceToHost, c->stream), "copy flux");
+    TRY(check_error_word(c));
+    double A = 0.0, L = 0.0;
+    for (int a = 0; a < c->M; ++a)
+        if (s < 0 || a == s) {
+            A += acc[a];
+            L += last[a];
+        }
+    if (inst) *inst = L;
+    if (avg) *avg = c->flux_count > 0 ? A / (double)c->flux_count : 0.0;
+    return LBE_OK;
+}
+
+lbe_status lbe_get_totals(lbe_ctx *c, double *mass, double *momentum, double *max_u) {
+    TRY(ready(c));
+    double *n, *J;
+    TRY(state_moments(c, &n, &J));
+    const long long N = c->g.N;
+    double r[2];
+    for (int a = 0; a < c->M && mass; ++a) {
+        LAUNCH(launch_reduce(n + (long long)a * N, N, (double *)c->partial.p, 1024, (double *)c->red_out.p, c->stream),
+               "reduce mass");
+        CK(cudaMemcpyAsync(r, c->red_out.p, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        mass[a] = r[0];
+    }
+    if (momentum) {
+        for (int k = 0; k < 3; ++k) {
+            double tot = 0.0;
+            for (int a = 0; a < c->M; ++a) {
+                LAUNCH(launch_reduce(J + ((long long)a * 3 + k) * N, N, (double *)c->partial.p, 1024,
+                                     (double *)c->red_out.p, c->stream),
+                       "reduce momentum");
+                CK(cudaMemcpyAsync(r, c->red_out.p, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+                CK(cudaStreamSynchronize(c->stream), "sync");
+                tot += r[0];
+            }
+            momentum[k] = tot;
+        }
+    }
+    if (max_u) {
+        double *sp = J + (long long)c->M * 3 * N;
+        LAUNCH(launch_velocity(c->M, N, -1, n, J, nullptr, sp, c->stream), "speed kernel");
+        LAUNCH(launch_reduce(sp, N, (double *)c->partial.p, 1024, (double *)c->red_out.p, c->stream), "reduce speed");
+        CK(cudaMemcpyAsync(r, c->red_out.p, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+        CK(cudaStreamSynchronize(c->stream), "sync");
+        *max_u = r[1];
+    }
+    return check_error_word(c);
+}
+
+lbe_status lbe_get_populations(lbe_ctx *c, int s, double *f, double *gq) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !f || !gq) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    const long long N = c->g.N;
+    Buf tmp;
+    TRY(dev_alloc(c, tmp, 2 * 8 * Q * N));
+    double *df = (double *)tmp.p, *dg = df + Q * N;
+    cudaError_t e = launch_stream_out(c->prec, c->g, (const uint32_t *)c->mask.p, c->pop[c->cur].p, s, c->n0[s], df,
+                                      dg, c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, df, 8 * Q * N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(gq, dg, 8 * Q * N, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "get populations");
+    return LBE_OK;
+}
+
+lbe_status lbe_set_populations(lbe_ctx *c, int s, const double *f, const double *gq) {
+    TRY(ready(c));
+    if (s < 0 || s >= c->M || !f || !gq) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null input");
+    const long long N = c->g.N;
+    if (c->prec == Prec::BF16 || c->prec == Prec::F16) {
+        // reference density: fluid-node mean of the zeroth moment
+        double sum = 0.0;
+        long long cnt = 0;
+        for (long long i = 0; i < N; ++i)
+            if (!c->solid_h[i]) {
+                double nn = 0.0;
+                for (int p = 0; p < Q; ++p) nn += f[(long long)p * N + i];
+                sum += nn;
+                ++cnt;
+            }
+        c->n0[s] = cnt > 0 ? sum / cnt : 0.0;
+        if (!(c->n0[s] > 0.0)) return fail(c, LBE_ERR_INVALID_ARG, "shifted storage needs a positive mean density");
+    }
+    Buf tmp;
+    TRY(dev_alloc(c, tmp, 2 * 8 * Q * N));
+    double *df = (double *)tmp.p, *dg = df + Q * N;
+    cudaError_t e = cudaMemcpyAsync(df, f, 8 * Q * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dg, gq, 8 * Q * N, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = launch_unstream(c->prec, c->g, (const uint32_t *)c->mask.p, df, dg, c->pop[c->cur].p, s, c->n0[s],
+                            c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dev_free(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "set populations");
+    reset_counters(c);
+    return LBE_OK;
+}
+
+lbe_status lbe_get_step_count(lbe_ctx *c, long long *steps) {
+    if (!c || !steps) return fail(c, LBE_ERR_INVALID_ARG, "null argument");
+    *steps = c->steps;
+    return LBE_OK;
+}
+
+lbe_status lbe_get_link_mask(lbe_ctx *c, uint32_t *out) {
+    TRY(ready(c));
+    if (!out) return fail(c, LBE_ERR_INVALID_ARG, "null output");
+    CK(cudaMemcpyAsync(out, c->mask.p, 4 * c->g.N, cudaMemcpyDeviceToHost, c->stream), "copy mask");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    return LBE_OK;
+}
+
+lbe_status lbe_shell(double sigma, int *e, int cap, int *count) {
+    if (!count) return fail(nullptr, LBE_ERR_INVALID_ARG, "null count");
+    int S = 0;
+    if (!integer_diameter(sigma, &S) || S < 0 || S > 16)
+        return fail(nullptr, LBE_ERR_UNSUPPORTED, "shells are tabulated for integer diameters 0..16");
+    int k = 0;
+    for (int z = -S; z <= S && S > 0; ++z)
+        for (int y = -S; y <= S; ++y)
+            for (int x = -S; x <= S; ++x)
+                if (in_shell(S, x, y, z)) {
+                    if (e && k < cap) {
+                        e[3 * k] = x;
+                        e[3 * k + 1] = y;
+                        e[3 * k + 2] = z;
+                    }
+                    ++k;
+                }
+    *count = k;
+    return LBE_OK;
+}
+
+lbe_status lbe_get_launch_count(lbe_ctx *c, long long *launches) {
+    if (!c || !launches) return fail(c, LBE_ERR_INVALID_ARG, "null argument");
+    *launches = c->launches;
+    return LBE_OK;
+}
+
+}  // extern "C"

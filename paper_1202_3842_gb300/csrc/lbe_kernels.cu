@@ -1,0 +1,726 @@
+// D3Q19 Lattice Boltzmann-Enskog kernels (sm_103a): geometry, force field,
+// population set/get, K1 density, K2 contact values, K4 fused DD-TR
+// collide-stream, moments and FP64 reductions.  The shell force (K3) is in
+// lbe_shell.cu.
+//
+// Population storage: [M][2 (f, g)][19][N] of the storage type S, holding the
+// post-collision populations f~*(r, t-1); the streamed populations of step t
+// are pulled: f~_p(r, t) = f~*_p(r - c_p, t-1), or f~*_{opp(p)}(r, t-1) when
+// the link is blocked (mid-point bounce-back, Sec. "Channel flow with a
+// bottleneck").  Link mask bit 0 marks a solid node, bit p a blocked link p.
+#include <math.h>
+
+#include <utility>
+
+#include "lbe_device.cuh"
+#include "lbe_launch.h"
+
+namespace lbe {
+
+constexpr int NT = 256;
+
+struct N0Vec {
+    double v[MAXS];
+};
+
+__device__ __forceinline__ long long pop_off(int a, int fg, int p, long long N) {
+    return ((long long)(a * 2 + fg) * Q + p) * N;
+}
+
+__device__ __forceinline__ void node_xyz(const Grid &g, long long i, int &x, int &y, int &z) {
+    x = (int)(i % g.nx);
+    long long r = i / g.nx;
+    y = (int)(r % g.ny);
+    z = (int)(r / g.ny);
+}
+
+// Linear offsets to the six neighbours with periodic wrap (a closed axis wraps
+// too; such links are masked, so the wrapped address is never used).
+struct NbrOff {
+    long long xm, xp, ym, yp, zm, zp;
+};
+__device__ __forceinline__ NbrOff nbr_offsets(const Grid &g, int x, int y, int z) {
+    NbrOff o;
+    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+    o.xm = (x > 0) ? -sx : (g.nx - 1) * sx;
+    o.xp = (x < g.nx - 1) ? sx : -(g.nx - 1) * sx;
+    o.ym = (y > 0) ? -sy : (g.ny - 1) * sy;
+    o.yp = (y < g.ny - 1) ? sy : -(g.ny - 1) * sy;
+    o.zm = (z > 0) ? -sz : (g.nz - 1) * sz;
+    o.zp = (z < g.nz - 1) ? sz : -(g.nz - 1) * sz;
+    return o;
+}
+// Offset of the source node r - c_p.
+template <int P>
+__device__ __forceinline__ long long src_off(const NbrOff &o) {
+    long long d = 0;
+    if constexpr (cx(P) == 1) d += o.xm;
+    if constexpr (cx(P) == -1) d += o.xp;
+    if constexpr (cy(P) == 1) d += o.ym;
+    if constexpr (cy(P) == -1) d += o.yp;
+    if constexpr (cz(P) == 1) d += o.zm;
+    if constexpr (cz(P) == -1) d += o.zp;
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+__global__ void k_link_mask(Grid g, const uint8_t *__restrict__ solid, uint32_t *__restrict__ mask) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    uint32_t m = solid[i] ? 1u : 0u;
+#pragma unroll
+    for (int p = 1; p < Q; ++p) {
+        int X = x - cx(p), Y = y - cy(p), Z = z - cz(p);
+        bool ok = wrap(X, g.nx, g.per[0]) && wrap(Y, g.ny, g.per[1]) && wrap(Z, g.nz, g.per[2]);
+        if (!ok || solid[X + (long long)g.nx * (Y + (long long)g.ny * Z)]) m |= (1u << p);
+    }
+    mask[i] = m;
+}
+
+cudaError_t launch_link_mask(const Grid &g, const uint8_t *solid, uint32_t *mask, cudaStream_t st) {
+    k_link_mask<<<(unsigned)((g.N + NT - 1) / NT), NT, 0, st>>>(g, solid, mask);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// force field F = -grad_h V + g  (isotropic D3Q19 gradient, FP64 arithmetic)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_force_field(Grid g, const double *__restrict__ V, const double *__restrict__ phi,
+                              const double *__restrict__ amp, double g0, double g1, double g2, T *__restrict__ F) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const double vi = V[i] + amp[i] * phi[i];
+    double gr[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int p = 1; p < Q; ++p) {
+        int X = x + cx(p), Y = y + cy(p), Z = z + cz(p);
+        bool ok = wrap(X, g.nx, g.per[0]) && wrap(Y, g.ny, g.per[1]) && wrap(Z, g.nz, g.per[2]);
+        double v = vi;
+        if (ok) {
+            long long j = X + (long long)g.nx * (Y + (long long)g.ny * Z);
+            v = V[j] + amp[j] * phi[j];
+        }
+        gr[0] += wq(p) * cx(p) * v;
+        gr[1] += wq(p) * cy(p) * v;
+        gr[2] += wq(p) * cz(p) * v;
+    }
+    F[i] = (T)(-3.0 * gr[0] + g0);
+    F[g.N + i] = (T)(-3.0 * gr[1] + g1);
+    F[2 * g.N + i] = (T)(-3.0 * gr[2] + g2);
+}
+
+cudaError_t launch_force_field(Prec p, const Grid &g, const double *V, const double *phi, const double *amp,
+                               const double gb[3], void *F, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    if (prec_fp64(p))
+        k_force_field<double><<<nb, NT, 0, st>>>(g, V, phi, amp, gb[0], gb[1], gb[2], (double *)F);
+    else
+        k_force_field<float><<<nb, NT, 0, st>>>(g, V, phi, amp, gb[0], gb[1], gb[2], (float *)F);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// populations: streamed FP64 <-> stored post-collision form
+// ---------------------------------------------------------------------------
+// post_p(s) = streamed_p(s + c_p) when s + c_p is a fluid node inside the
+// lattice, else streamed_{opp(p)}(s) (the population bounced back at s).
+template <typename S, typename T>
+__global__ void k_unstream(Grid g, const uint32_t *__restrict__ mask, const double *__restrict__ f,
+                           const double *__restrict__ gq, S *__restrict__ pop, int a, T n0) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    node_xyz(g, s, x, y, z);
+    const bool solid = mask[s] & 1u;
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+        double fv = 0.0, gv = 0.0;
+        if (!solid) {
+            int X = x + cx(p), Y = y + cy(p), Z = z + cz(p);
+            bool ok = wrap(X, g.nx, g.per[0]) && wrap(Y, g.ny, g.per[1]) && wrap(Z, g.nz, g.per[2]);
+            long long t = ok ? X + (long long)g.nx * (Y + (long long)g.ny * Z) : 0;
+            if (ok && !(mask[t] & 1u)) {
+                fv = f[(long long)p * g.N + t];
+                gv = gq[(long long)p * g.N + t];
+            } else {
+                fv = f[(long long)opp(p) * g.N + s];
+                gv = gq[(long long)opp(p) * g.N + s];
+            }
+        }
+        const T wn0 = (T)wq(p) * n0;
+        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)fv, wn0);
+        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)gv, wn0);
+    }
+}
+
+// Rest state: streamed_p(r) = w_p n(r) on fluid nodes.
+template <typename S, typename T>
+__global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const double *__restrict__ n,
+                             S *__restrict__ pop, int a, T n0) {
+    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.N) return;
+    int x, y, z;
+    node_xyz(g, s, x, y, z);
+    const bool solid = mask[s] & 1u;
+#pragma unroll
+    for (int p = 0; p < Q; ++p) {
+        double v = 0.0;
+        if (!solid) {
+            int X = x + cx(p), Y = y + cy(p), Z = z + cz(p);
+            bool ok = wrap(X, g.nx, g.per[0]) && wrap(Y, g.ny, g.per[1]) && wrap(Z, g.nz, g.per[2]);
+            long long t = ok ? X + (long long)g.nx * (Y + (long long)g.ny * Z) : 0;
+            v = (ok && !(mask[t] & 1u)) ? wq(p) * n[t] : wq(p) * n[s];
+        }
+        const T wn0 = (T)wq(p) * n0;
+        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)v, wn0);
+        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)v, wn0);
+    }
+}
+
+template <typename S, typename T, int P>
+__device__ __forceinline__ T pull(const S *__restrict__ fg_base, long long N, long long i, const NbrOff &o,
+                                  uint32_t m, T n0) {
+    // fg_base points at population 0 of this species' f (or g) block
+    const T wn0 = (T)wq(P) * n0;
+    if (m & (1u << P)) return Store<S, T>::load(fg_base + (long long)opp(P) * N + i, wn0);
+    return Store<S, T>::load(fg_base + (long long)P * N + i + src_off<P>(o), wn0);
+}
+
+template <typename S, typename T>
+__global__ void k_stream_out(Grid g, const uint32_t *__restrict__ mask, const S *__restrict__ pop, int a, T n0,
+                             double *__restrict__ f, double *__restrict__ gq) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const uint32_t m = mask[i];
+    const NbrOff o = nbr_offsets(g, x, y, z);
+    const S *fb = pop + pop_off(a, 0, 0, g.N);
+    const S *gb = pop + pop_off(a, 1, 0, g.N);
+    auto body = [&](auto Pc) {
+        constexpr int P = decltype(Pc)::value;
+        double fv = 0.0, gv = 0.0;
+        if (!(m & 1u)) {
+            fv = (double)pull<S, T, P>(fb, g.N, i, o, m, n0);
+            gv = (double)pull<S, T, P>(gb, g.N, i, o, m, n0);
+        }
+        f[(long long)P * g.N + i] = fv;
+        gq[(long long)P * g.N + i] = gv;
+    };
+    [&]<int... P>(std::integer_sequence<int, P...>) { (body(std::integral_constant<int, P>{}), ...); }
+    (std::make_integer_sequence<int, Q>{});
+}
+
+#define LBE_DISPATCH_PREC(p, CALL)                                       \
+    switch (p) {                                                         \
+        case Prec::F64: { using S = double; using T = double; CALL; break; }      \
+        case Prec::F32: { using S = float; using T = float; CALL; break; }        \
+        case Prec::BF16: { using S = __nv_bfloat16; using T = float; CALL; break; } \
+        case Prec::F16: { using S = __half; using T = float; CALL; break; }       \
+    }
+
+cudaError_t launch_unstream(Prec p, const Grid &g, const uint32_t *mask, const double *f, const double *gq,
+                            void *pop, int a, double n0, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    LBE_DISPATCH_PREC(p, (k_unstream<S, T><<<nb, NT, 0, st>>>(g, mask, f, gq, (S *)pop, a, (T)n0)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
+                              double n0, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    LBE_DISPATCH_PREC(p, (k_rest_state<S, T><<<nb, NT, 0, st>>>(g, mask, n, (S *)pop, a, (T)n0)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const void *pop, int a, double n0,
+                              double *f, double *gq, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    LBE_DISPATCH_PREC(p, (k_stream_out<S, T><<<nb, NT, 0, st>>>(g, mask, (const S *)pop, a, (T)n0, f, gq)));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K1: density n^a(r) = sum_p f~_p(r) (streamed), 0 on solid nodes, written to
+// the padded stencil field with its periodic images.
+// ---------------------------------------------------------------------------
+template <typename S, typename T, bool SOLID>
+__global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ pop, const uint32_t *__restrict__ mask,
+                                                int M, N0Vec n0v, T *__restrict__ npad, int *err) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const uint32_t m = SOLID ? mask[i] : 0u;
+    const NbrOff o = nbr_offsets(g, x, y, z);
+    for (int a = 0; a < M; ++a) {
+        T n = (T)0;
+        if (!(m & 1u)) {
+            const S *fb = pop + pop_off(a, 0, 0, g.N);
+            const T n0 = (T)n0v.v[a];
+            [&]<int... P>(std::integer_sequence<int, P...>) {
+                ((n += pull<S, T, P>(fb, g.N, i, o, m, n0)), ...);
+            }(std::make_integer_sequence<int, Q>{});
+            if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
+        }
+        write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);
+    }
+}
+
+cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, int M,
+                           const double *n0, void *npad, int *err, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    N0Vec n0v;
+    for (int a = 0; a < MAXS; ++a) n0v.v[a] = a < M ? n0[a] : 0.0;
+    LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K2: contact values.  n-bar_b = mean of n_b over the ball |d| <= sigma_b/2,
+// xi_k = (pi/6) sum_b sigma_b^k n-bar_b, and the Boublik-Mansoori-Carnahan-
+// Starling-Leland contact value g_ab = 1/(1-xi3) + 3 s xi2/(1-xi3)^2
+// + 2 s^2 xi2^2/(1-xi3)^3 with s = sigma_a sigma_b/(sigma_a + sigma_b).
+// Writes g_ab [M][M][N] and the padded product g_ab * n_b [M][M][P].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) k_contact(Grid g, ContactParams cp, const int *__restrict__ ball,
+                                                const T *__restrict__ npad, T *__restrict__ gab,
+                                                T *__restrict__ gnpad, int *err) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const long long pc = pidx(g, x, y, z);
+    T xi2 = 0, xi3 = 0;
+    T nloc[MAXS];
+    for (int b = 0; b < cp.M; ++b) {
+        const T *nb = npad + (long long)b * g.P + pc;
+        const int k0 = cp.ball_start[b], k1 = k0 + cp.ball_count[b];
+        T acc = 0;
+        for (int k = k0; k < k1; ++k) acc += __ldg(nb + __ldg(ball + k));
+        const T nbar = acc / (T)cp.ball_count[b];
+        xi2 += (T)cp.xi2c[b] * nbar;
+        xi3 += (T)cp.xi3c[b] * nbar;
+        nloc[b] = nb[0];
+    }
+    const T i1 = (T)1 / ((T)1 - xi3);
+    if (!(xi3 < (T)1)) atomicOr(err, ERR_PACKING);
+    for (int a = 0; a < cp.M; ++a)
+        for (int b = 0; b < cp.M; ++b) {
+            const T s = (T)cp.s_ab[a][b];
+            const T gv = i1 + (T)3 * s * xi2 * i1 * i1 + (T)2 * s * s * xi2 * xi2 * i1 * i1 * i1;
+            if (!isfinite(gv)) atomicOr(err, ERR_PACKING);
+            gab[(long long)(a * cp.M + b) * g.N + i] = gv;
+            write_padded<T>(g, gnpad + (long long)(a * cp.M + b) * g.P, x, y, z, gv * nloc[b]);
+        }
+}
+
+cudaError_t launch_contact(bool fp64, const Grid &g, const ContactParams &cp, const int *ball, const void *npad,
+                           void *gab, void *gnpad, int *err, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    if (fp64)
+        k_contact<double><<<nb, NT, 0, st>>>(g, cp, ball, (const double *)npad, (double *)gab, (double *)gnpad, err);
+    else
+        k_contact<float><<<nb, NT, 0, st>>>(g, cp, ball, (const float *)npad, (float *)gab, (float *)gnpad, err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// K4: fused moments + DD-TR collision + streaming (Sec. "Hard sphere fluid
+// mixture in a potential well"):
+//   n = sum f~, Pi~ = sum g~, J~ = sum c g~;
+//   printed recovery:    J = J~ + (C + nF)/2,  Pi = Pi~ - C.u^a/2;
+//   consistent recovery: J = J~ + nF/2,        Pi = Pi~ + beta C.u^a/2;
+//   u^a = J/n, u = sum J / sum n;
+//   f_eq = w [n + n u^a.H1 + n (2 u^a u - u u):H2],  g_eq = same with Pi first;
+//   S_f = w (C + nF).[H1 + 2 H2.u^a];
+//   S_g = w { C.[u^a/v_T^2 + 4 H2.u^a] + nF.[H1 + 2 H2.u^a] };
+//   f~* = f~ + [omega (f_eq - f~) + S_f] / (1 + omega/2)   (same for g~).
+// With v_T^2 = 1/3 the Hermite contractions expand to the scalar forms below
+// (A, B isotropic parts; sf0 = -3 (C + nF).u^a is shared by S_f and S_g).
+// ---------------------------------------------------------------------------
+template <typename T, int P>
+__device__ __forceinline__ T cdot(const T *v) {
+    T r = (T)0;
+    if constexpr (cx(P) == 1) r += v[0];
+    if constexpr (cx(P) == -1) r -= v[0];
+    if constexpr (cy(P) == 1) r += v[1];
+    if constexpr (cy(P) == -1) r -= v[1];
+    if constexpr (cz(P) == 1) r += v[2];
+    if constexpr (cz(P) == -1) r -= v[2];
+    return r;
+}
+
+template <typename S, typename T, int M>
+struct NodeState {
+    T f[M][Q], g[M][Q];
+    T n[M], Pi[M], J[M][3], C[M][3], nF[M][3], ua[M][3];
+    T u[3];
+};
+
+template <typename S, typename T, int M>
+__device__ __forceinline__ void load_moments(const Grid &g, const S *__restrict__ src, const T *__restrict__ C,
+                                             const T *__restrict__ F, const StepParams &sp, long long i,
+                                             const NbrOff &o, uint32_t m, NodeState<S, T, M> &st) {
+    T ntot = 0, Jtot[3] = {0, 0, 0};
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const T n0 = (T)sp.sp[a].n0;
+        const S *fb = src + pop_off(a, 0, 0, g.N);
+        const S *gb = src + pop_off(a, 1, 0, g.N);
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            ((st.f[a][P] = pull<S, T, P>(fb, g.N, i, o, m, n0)), ...);
+            ((st.g[a][P] = pull<S, T, P>(gb, g.N, i, o, m, n0)), ...);
+        }(std::make_integer_sequence<int, Q>{});
+        T n = 0, Pit = 0, Jt[3] = {0, 0, 0};
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            ((n += st.f[a][P]), ...);
+            ((Pit += st.g[a][P]), ...);
+            ((Jt[0] += (T)cx(P) * st.g[a][P]), ...);
+            ((Jt[1] += (T)cy(P) * st.g[a][P]), ...);
+            ((Jt[2] += (T)cz(P) * st.g[a][P]), ...);
+        }(std::make_integer_sequence<int, Q>{});
+        const T *Ca = C + (long long)a * 3 * g.N + i;
+        const T *Fa = F + (long long)a * 3 * g.N + i;
+        T Cu = 0;
+        const T inv_n = n > (T)0 ? (T)1 / n : (T)0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            st.C[a][c] = Ca[(long long)c * g.N];
+            st.nF[a][c] = n * Fa[(long long)c * g.N];
+            st.J[a][c] = sp.consistent ? Jt[c] + (T)0.5 * st.nF[a][c]
+                                       : Jt[c] + (T)0.5 * (st.C[a][c] + st.nF[a][c]);
+            st.ua[a][c] = st.J[a][c] * inv_n;
+            Cu += st.C[a][c] * st.ua[a][c];
+            Jtot[c] += st.J[a][c];
+        }
+        st.n[a] = n;
+        st.Pi[a] = sp.consistent ? Pit + (T)1.5 * Cu : Pit - (T)0.5 * Cu;
+        ntot += n;
+    }
+    const T inv_tot = ntot > (T)0 ? (T)1 / ntot : (T)0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) st.u[c] = Jtot[c] * inv_tot;
+}
+
+__device__ __forceinline__ int plane_index(const Grid &g, int axis, int x, int y, int z) {
+    return axis == 0 ? y + g.ny * z : (axis == 1 ? x + g.nx * z : x + g.nx * y);
+}
+
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ src, S *__restrict__ dst,
+                                                const uint32_t *__restrict__ mask, const T *__restrict__ C,
+                                                const T *__restrict__ F, StepParams sp,
+                                                double *__restrict__ flux_buf) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const uint32_t m = mask[i];
+    const int coord = sp.flux_axis == 0 ? x : (sp.flux_axis == 1 ? y : z);
+    const bool on_plane = sp.flux_axis >= 0 && coord == sp.flux_plane;
+    const int psize = sp.flux_axis == 0 ? g.ny * g.nz : (sp.flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
+    if (m & 1u) {  // solid node: no fluid
+        if (on_plane)
+            for (int a = 0; a < M; ++a) flux_buf[(long long)a * psize + plane_index(g, sp.flux_axis, x, y, z)] = 0.0;
+        return;
+    }
+    const NbrOff o = nbr_offsets(g, x, y, z);
+    NodeState<S, T, M> st;
+    load_moments<S, T, M>(g, src, C, F, sp, i, o, m, st);
+    if (on_plane) {
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+            flux_buf[(long long)a * psize + plane_index(g, sp.flux_axis, x, y, z)] = (double)st.J[a][sp.flux_axis];
+    }
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        const T n = st.n[a];
+        const T *ua = st.ua[a];
+        const T uau = ua[0] * st.u[0] + ua[1] * st.u[1] + ua[2] * st.u[2];
+        const T uu = st.u[0] * st.u[0] + st.u[1] * st.u[1] + st.u[2] * st.u[2];
+        const T iso = (T)1.5 * n * ((T)2 * uau - uu);
+        const T A = n - iso;
+        const T B = st.Pi[a] - iso;
+        T X[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) X[c] = st.C[a][c] + st.nF[a][c];
+        const T sf0 = (T)-3 * (X[0] * ua[0] + X[1] * ua[1] + X[2] * ua[2]);
+        const T om = (T)sp.sp[a].omega_eff;
+        const T inv = (T)sp.sp[a].inv;
+        const T n0 = (T)sp.sp[a].n0;
+        S *fo = dst + pop_off(a, 0, 0, g.N) + i;
+        S *go = dst + pop_off(a, 1, 0, g.N) + i;
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            (
+                [&] {
+                    constexpr T w = (T)wq(P);
+                    const T cua = cdot<T, P>(ua);
+                    const T cu = cdot<T, P>(st.u);
+                    const T cX = cdot<T, P>(X);
+                    const T cY = cdot<T, P>(st.nF[a]);
+                    const T cC = cdot<T, P>(st.C[a]);
+                    const T t1 = (T)3 * n * cua + (T)4.5 * n * ((T)2 * cua * cu - cu * cu);
+                    const T feq = w * (A + t1);
+                    const T geq = w * (B + t1);
+                    const T Sf = w * (sf0 + (T)3 * cX + (T)9 * cX * cua);
+                    const T Sg = w * (sf0 + (T)3 * cY + (T)18 * cC * cua + (T)9 * cY * cua);
+                    const T fs = st.f[a][P] + om * (feq - st.f[a][P]) + inv * Sf;
+                    const T gs = st.g[a][P] + om * (geq - st.g[a][P]) + inv * Sg;
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * n0);
+                    Store<S, T>::store(go + (long long)P * g.N, gs, w * n0);
+                }(),
+                ...);
+        }(std::make_integer_sequence<int, Q>{});
+    }
+}
+
+template <typename S, typename T>
+static cudaError_t collide_m(int M, const Grid &g, const void *src, void *dst, const uint32_t *mask, const void *C,
+                             const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    switch (M) {
+        case 1:
+            k_collide<S, T, 1><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
+                                                  flux_buf);
+            break;
+        case 2:
+            k_collide<S, T, 2><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
+                                                  flux_buf);
+            break;
+        case 3:
+            k_collide<S, T, 3><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
+                                                  flux_buf);
+            break;
+        case 4:
+            k_collide<S, T, 4><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
+                                                  flux_buf);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, const void *C,
+                           const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    LBE_DISPATCH_PREC(p, (e = collide_m<S, T>(sp.M, g, src, dst, mask, C, F, sp, flux_buf, st)));
+    return e;
+}
+
+// Moments of the current state for the getters: n [M][N], J [M][3][N] (FP64).
+template <typename S, typename T, int M>
+__global__ void __launch_bounds__(NT) k_moments(Grid g, const S *__restrict__ src, const uint32_t *__restrict__ mask,
+                                                const T *__restrict__ C, const T *__restrict__ F, StepParams sp,
+                                                double *__restrict__ nout, double *__restrict__ Jout) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const uint32_t m = mask[i];
+    if (m & 1u) {
+        for (int a = 0; a < M; ++a) {
+            nout[(long long)a * g.N + i] = 0.0;
+            for (int c = 0; c < 3; ++c) Jout[((long long)a * 3 + c) * g.N + i] = 0.0;
+        }
+        return;
+    }
+    const NbrOff o = nbr_offsets(g, x, y, z);
+    NodeState<S, T, M> st;
+    load_moments<S, T, M>(g, src, C, F, sp, i, o, m, st);
+    for (int a = 0; a < M; ++a) {
+        nout[(long long)a * g.N + i] = (double)st.n[a];
+        for (int c = 0; c < 3; ++c) Jout[((long long)a * 3 + c) * g.N + i] = (double)st.J[a][c];
+    }
+}
+
+template <typename S, typename T>
+static cudaError_t moments_m(int M, const Grid &g, const void *pop, const uint32_t *mask, const void *C, const void *F,
+                             const StepParams &sp, double *n, double *J, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    switch (M) {
+        case 1: k_moments<S, T, 1><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, (const T *)C, (const T *)F, sp, n, J); break;
+        case 2: k_moments<S, T, 2><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, (const T *)C, (const T *)F, sp, n, J); break;
+        case 3: k_moments<S, T, 3><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, (const T *)C, (const T *)F, sp, n, J); break;
+        case 4: k_moments<S, T, 4><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, (const T *)C, (const T *)F, sp, n, J); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *C,
+                           const void *F, const StepParams &sp, double *n, double *J, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    LBE_DISPATCH_PREC(p, (e = moments_m<S, T>(sp.M, g, pop, mask, C, F, sp, n, J, st)));
+    return e;
+}
+
+// ---------------------------------------------------------------------------
+// K5 and FP64 reductions (deterministic: fixed per-thread order, fixed tree).
+// ---------------------------------------------------------------------------
+template <int NTH>
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < NTH / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    }
+    __syncthreads();
+    return v;  // valid in thread 0
+}
+template <int NTH>
+__device__ __forceinline__ double block_max(double v, double *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < NTH / 32 ? sh[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    }
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) k_flux_reduce(int M, int psize, const double *__restrict__ buf,
+                                                      double *__restrict__ acc, double *__restrict__ last) {
+    __shared__ double sh[32];
+    for (int a = 0; a < M; ++a) {
+        double s = 0.0;
+        for (int k = threadIdx.x; k < psize; k += 1024) s += buf[(long long)a * psize + k];
+        s = block_sum<1024>(s, sh);
+        if (threadIdx.x == 0) {
+            acc[a] += s;
+            last[a] = s;
+        }
+    }
+}
+
+cudaError_t launch_flux_reduce(int M, int plane_size, const double *buf, double *acc, double *last,
+                               cudaStream_t st) {
+    k_flux_reduce<<<1, 1024, 0, st>>>(M, plane_size, buf, acc, last);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(NT) k_reduce_partial(const double *__restrict__ x, long long n, long long chunk,
+                                                       double *__restrict__ partial) {
+    __shared__ double sh[32];
+    const long long b0 = (long long)blockIdx.x * chunk;
+    const long long b1 = min(n, b0 + chunk);
+    double s = 0.0, mx = 0.0;
+    for (long long k = b0 + threadIdx.x; k < b1; k += NT) {
+        s += x[k];
+        mx = fmax(mx, fabs(x[k]));
+    }
+    s = block_sum<NT>(s, sh);
+    mx = block_max<NT>(mx, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = s;
+        partial[2 * blockIdx.x + 1] = mx;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_final(const double *__restrict__ partial, int np,
+                                                       double *__restrict__ out) {
+    __shared__ double sh[32];
+    double s = 0.0, mx = 0.0;
+    for (int k = threadIdx.x; k < np; k += 1024) {
+        s += partial[2 * k];
+        mx = fmax(mx, partial[2 * k + 1]);
+    }
+    s = block_sum<1024>(s, sh);
+    mx = block_max<1024>(mx, sh);
+    if (threadIdx.x == 0) {
+        out[0] = s;
+        out[1] = mx;
+    }
+}
+
+cudaError_t launch_reduce(const double *x, long long n, double *partial, int npartial, double *out,
+                          cudaStream_t st) {
+    long long chunk = (n + npartial - 1) / npartial;
+    if (chunk < 1) chunk = 1;
+    int nb = (int)((n + chunk - 1) / chunk);
+    if (nb < 1) nb = 1;
+    k_reduce_partial<<<nb, NT, 0, st>>>(x, n, chunk, partial);
+    k_reduce_final<<<1, 1024, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_to_f64(const T *__restrict__ src, long long n, double *__restrict__ dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (double)src[i];
+}
+
+cudaError_t launch_to_f64(bool fp64, const void *src, long long n, double *dst, cudaStream_t st) {
+    unsigned nb = (unsigned)((n + NT - 1) / NT);
+    if (fp64)
+        k_to_f64<double><<<nb, NT, 0, st>>>((const double *)src, n, dst);
+    else
+        k_to_f64<float><<<nb, NT, 0, st>>>((const float *)src, n, dst);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_unpad(Grid g, const T *__restrict__ pad, double *__restrict__ dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    dst[i] = (double)pad[pidx(g, x, y, z)];
+}
+
+cudaError_t launch_unpad(bool fp64, const Grid &g, const void *pad, double *dst, cudaStream_t st) {
+    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+    if (fp64)
+        k_unpad<double><<<nb, NT, 0, st>>>(g, (const double *)pad, dst);
+    else
+        k_unpad<float><<<nb, NT, 0, st>>>(g, (const float *)pad, dst);
+    return cudaGetLastError();
+}
+
+// Velocity u = sum_sel J / sum_sel n (sel: species s, or all for s < 0), 0 where n = 0.
+__global__ void k_velocity(int M, long long N, int s, const double *__restrict__ n, const double *__restrict__ J,
+                           double *__restrict__ u, double *__restrict__ speed) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double nn = 0.0, j0 = 0.0, j1 = 0.0, j2 = 0.0;
+    for (int a = 0; a < M; ++a) {
+        if (s >= 0 && a != s) continue;
+        nn += n[(long long)a * N + i];
+        j0 += J[((long long)a * 3 + 0) * N + i];
+        j1 += J[((long long)a * 3 + 1) * N + i];
+        j2 += J[((long long)a * 3 + 2) * N + i];
+    }
+    const double r = nn > 0.0 ? 1.0 / nn : 0.0;
+    if (u) {
+        u[i] = j0 * r;
+        u[N + i] = j1 * r;
+        u[2 * N + i] = j2 * r;
+    }
+    if (speed) speed[i] = sqrt(j0 * j0 + j1 * j1 + j2 * j2) * r;
+}
+
+cudaError_t launch_velocity(int M, long long N, int s, const double *n, const double *J, double *u, double *speed,
+                            cudaStream_t st) {
+    k_velocity<<<(unsigned)((N + NT - 1) / NT), NT, 0, st>>>(M, N, s, n, J, u, speed);
+    return cudaGetLastError();
+}
+
+}  // namespace lbe

@@ -1,0 +1,101 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbe_device.cuh"
+
+namespace lbe {
+
+// Storage of the populations: [M][2 (f, g)][19][N] elements of the storage type.
+enum class Prec : int { F64 = 0, F32 = 1, BF16 = 2, F16 = 3 };
+
+inline int prec_bytes(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
+inline bool prec_fp64(Prec p) { return p == Prec::F64; }
+
+// Per-species constants of the collision.
+struct SpeciesConst {
+    double omega_eff;  // omega h / (1 + omega h / 2) = 1/tau
+    double inv;        // h / (1 + omega h / 2)
+    double n0;         // reference density of the shifted 16-bit storage
+};
+
+struct StepParams {
+    int M;
+    int consistent;      // moment recovery: 0 printed, 1 map-consistent
+    int flux_axis;       // -1: no flux plane
+    int flux_plane;
+    SpeciesConst sp[MAXS];
+};
+
+struct ContactParams {
+    int M;
+    int npairs;
+    double sigma[MAXS];
+    double s_ab[MAXS][MAXS];   // sigma_a sigma_b / (sigma_a + sigma_b)
+    double xi2c[MAXS];         // (pi/6) sigma_b^2
+    double xi3c[MAXS];         // (pi/6) sigma_b^3
+    int ball_start[MAXS];      // first entry of species b in the ball offset table
+    int ball_count[MAXS];
+};
+
+struct ShellLaunch {
+    const Grid *grid;
+    const CUtensorMap *map_n;
+    const CUtensorMap *map_gn;
+    const void *npad_a;
+    const void *g_ab;
+    void *Cout;
+    double coef;
+    int accumulate;
+    int *err;
+};
+
+// Geometry
+cudaError_t launch_link_mask(const Grid &g, const uint8_t *solid, uint32_t *mask, cudaStream_t st);
+// Force field F^a = -grad_h (V^a + amp*phi) + g^a, stored as T [3][N].
+cudaError_t launch_force_field(Prec p, const Grid &g, const double *V, const double *phi, const double *amp,
+                               const double gbody[3], void *F, cudaStream_t st);
+// Populations: [19][N] FP64 streamed form <-> storage (post-collision form) of species a.
+cudaError_t launch_unstream(Prec p, const Grid &g, const uint32_t *mask, const double *f, const double *gq,
+                            void *pop, int a, double n0, cudaStream_t st);
+cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const void *pop, int a, double n0,
+                              double *f, double *gq, cudaStream_t st);
+cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
+                              double n0, cudaStream_t st);
+// K1: density (pulled zeroth moment) of every species into the padded field.
+cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, int M,
+                           const double *n0, void *npad, int *err, cudaStream_t st);
+// K2: ball averages, BMCSL contact values g_ab [M][M][N] and padded g_ab*n_b [M][M][P].
+// ball: padded linear offsets of every species' averaging ball (see ContactParams).
+cudaError_t launch_contact(bool fp64, const Grid &g, const ContactParams &cp, const int *ball, const void *npad,
+                           void *gab, void *gnpad, int *err, cudaStream_t st);
+// K3: shell force of one ordered pair.
+cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st);
+bool shell_supported(bool fp64, int S);
+void shell_box(bool fp64, int S, int *bx, int *by);
+int half_shell_host(int S, int *e, int cap);
+// K4: fused moments + DD-TR collision + pull streaming.
+cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask,
+                           const void *C, const void *F, const StepParams &sp, double *flux_buf,
+                           cudaStream_t st);
+// Moments of the current state (FP64 out): n [M][N], J [M][3][N].
+cudaError_t launch_moments(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *C,
+                           const void *F, const StepParams &sp, double *n, double *J, cudaStream_t st);
+// K5: flux of the step: sum of the plane buffer [M][plane] into acc[M] (+=) and last[M] (=).
+cudaError_t launch_flux_reduce(int M, int plane_size, const double *buf, double *acc, double *last,
+                               cudaStream_t st);
+// Deterministic FP64 reductions: out[0] = sum x[0..n), out[1] = max |x|.
+cudaError_t launch_reduce(const double *x, long long n, double *partial, int npartial, double *out,
+                          cudaStream_t st);
+// u [3][N] = J/n summed over species s (all for s < 0); speed [N] = |u| (either may be NULL).
+cudaError_t launch_velocity(int M, long long N, int s, const double *n, const double *J, double *u, double *speed,
+                            cudaStream_t st);
+// Convert a compute-precision field to FP64.
+cudaError_t launch_to_f64(bool fp64, const void *src, long long n, double *dst, cudaStream_t st);
+// Copy the interior of a padded field to a dense FP64 array.
+cudaError_t launch_unpad(bool fp64, const Grid &g, const void *pad, double *dst, cudaStream_t st);
+
+}  // namespace lbe

@@ -1,0 +1,79 @@
+// Compile-time contact shells and the tile geometry of the shell-force kernel.
+#pragma once
+
+#include <utility>
+
+namespace lbe {
+
+// Contact shell of integer diameter S (Appendix, hard-sphere C^{alpha,mf}: the
+// integral over unit vectors k^ at distance sigma becomes a sum over the lattice
+// vectors e with S - 1/2 <= |e| < S + 1/2, i.e. S^2 - S + 1 <= |e|^2 <= S^2 + S).
+// Only one vector of each +-e pair is listed ("half shell"): the kernel sums
+// e^ [a(r+e) - a(r-e)], which is exact because the shell is symmetric.
+__host__ __device__ constexpr bool in_shell(int S, int x, int y, int z) {
+    int r2 = x * x + y * y + z * z;
+    return r2 >= S * S - S + 1 && r2 <= S * S + S;
+}
+__host__ __device__ constexpr bool positive_half(int x, int y, int z) {
+    return z > 0 || (z == 0 && (y > 0 || (y == 0 && x > 0)));
+}
+__host__ __device__ constexpr int half_shell_count(int S) {
+    int c = 0;
+    for (int z = -S; z <= S; ++z)
+        for (int y = -S; y <= S; ++y)
+            for (int x = -S; x <= S; ++x)
+                if (in_shell(S, x, y, z) && positive_half(x, y, z)) ++c;
+    return c;
+}
+
+template <int K>
+struct HalfShell {
+    int e[K > 0 ? K : 1][3];
+};
+
+template <int S>
+__host__ __device__ constexpr HalfShell<half_shell_count(S)> make_half_shell() {
+    HalfShell<half_shell_count(S)> h{};
+    int c = 0;
+    for (int z = -S; z <= S; ++z)
+        for (int y = -S; y <= S; ++y)
+            for (int x = -S; x <= S; ++x)
+                if (in_shell(S, x, y, z) && positive_half(x, y, z)) {
+                    h.e[c][0] = x;
+                    h.e[c][1] = y;
+                    h.e[c][2] = z;
+                    ++c;
+                }
+    return h;
+}
+
+// sqrt of a positive integer at compile time: Newton's method started above
+// the root, stopped when an iterate no longer decreases; the result is within
+// one unit in the last place of the true root.
+__host__ __device__ constexpr double ct_sqrt(double v) {
+    double x = v > 1.0 ? v : 1.0;
+    for (int i = 0; i < 200; ++i) {
+        double nx = 0.5 * (x + v / x);
+        if (!(nx < x)) break;
+        x = nx;
+    }
+    return x;
+}
+
+// Tile of the shell kernel: 32 x TY outputs per z-plane, marching LZ planes in z.
+template <typename T, int S>
+struct ShellTile {
+    static constexpr int A = 16 / (int)sizeof(T);  // TMA x-alignment in elements
+    static constexpr int TX = 32;
+    static constexpr int TY = (sizeof(T) == 8 && S >= 5) ? 4 : 8;
+    static constexpr int BX = ((TX + 2 * S + A - 1) + A - 1) / A * A;  // box width incl. alignment slack
+    static constexpr int BY = TY + 2 * S;
+    static constexpr int R = 2 * S + 2;  // ring slots: 2S+1 planes in use + 1 in flight
+    static constexpr int PLANE = BX * BY;  // elements of one field plane
+    static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
+    static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;  // density plane + g*n plane
+    static constexpr int SMEM = R * SLOT_BYTES + 128 /*barriers*/ + 128 /*alignment*/;
+    static constexpr int LZ = 32;
+};
+
+}  // namespace lbe
