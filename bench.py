@@ -1,0 +1,445 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the DD-TR Lattice Boltzmann-Enskog step on GB300.
+
+One "step" is one full time step of the hot path (density K1, contact values
+K2, mean-field shell force K3, fused moments + DD-TR collision + streaming K4)
+over the whole lattice.  The default workload is the one-component spherical
+well at production size: D3Q19 256^3 periodic, sigma = 6, packing 0.3,
+Gaussian well 2 kT / radius 24, tau = 0.8, FP32 populations.
+
+Prints one JSON line (rank 0).  Metric: Enskog-LB MLUPS per species =
+nodes * species * steps / (time * 1e6), aggregated over all ranks (each rank
+runs an independent replica: the method runs on one GPU and has no
+cross-replica exchange, so N > 1 is weak scaling).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload well256] [--prec fp32]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on a bounded sample
+"""
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK_HBM_GBS = 6800.0
+SMS = 152
+FP32_LANES_PER_SM = 128
+QPOP = 19
+
+WORKLOAD_TEXT = {
+    "well256": "D3Q19 256^3 periodic, 1 species, sigma 6, packing 0.3 (+-1% noise, seed 1202), Gaussian well "
+               "2 kT radius 24 at the centre, tau 0.8",
+    "well160": "D3Q19 160^3 periodic, 1 species, sigma 6, packing 0.3 (+-1% noise, seed 1202), Gaussian well "
+               "2 kT radius 15 at the centre, tau 0.8",
+    "well24": "D3Q19 24^3 periodic, 1 species, sigma 3, packing 0.2 (+-1% noise, seed 1202), Gaussian well "
+              "1 kT radius 5, tau 1",
+    "channel512": "D3Q19 512x128x128, periodic x, walls y/z, slit constriction width 16 length 64, sigma 4/6 "
+                  "equal mole fraction, packing 0.25, tau 1/1, body force 1e-6 along x",
+    "channel256adj": "D3Q19 256x64x64, periodic x, walls y/z, constriction width 12 length 32, sigma 4/6, "
+                     "packing 0.25, wall potential 1 kT",
+}
+DTYPE = {"fp64": "f64", "fp32": "f32", "bf16": "f32 (bf16 storage)", "fp16": "f32 (fp16 storage)"}
+STORE_BYTES = {"fp64": 8, "fp32": 4, "bf16": 2, "fp16": 2}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=300)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="well256")
+    p.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "fp16"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.path = tempfile.mktemp(prefix="lbe_clocks_", suffix=".csv")
+        self.proc = None
+        self.device = device
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.device)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self, which):
+        setattr(self, which, time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = list(csv.reader(open(self.path)))
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        sm, mx, reasons, all_sm = [], None, set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 10:
+                continue
+            try:
+                ts = time.mktime(time.strptime(r[0].strip().split(".")[0], "%Y/%m/%d %H:%M:%S"))
+                s = float(r[2])
+                mx = float(r[3])
+            except Exception:
+                continue
+            all_sm.append(s)
+            if self.t0 is not None and not (self.t0 - 1.0 <= ts <= self.t1 + 1.0):
+                continue
+            sm.append(s)
+            for k, nm in enumerate(names):
+                if r[6 + k].strip().lower().startswith("active"):
+                    reasons.add(nm)
+        use = sm if sm else all_sm
+        return {"sm_mhz": statistics.median(use) if use else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(use)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per launch
+# ---------------------------------------------------------------------------
+def half_shell(S):
+    out = []
+    for z in range(-S, S + 1):
+        for y in range(-S, S + 1):
+            for x in range(-S, S + 1):
+                r2 = x * x + y * y + z * z
+                if S * S - S + 1 <= r2 <= S * S + S and (z > 0 or (z == 0 and (y > 0 or (y == 0 and x > 0)))):
+                    out.append((x, y, z))
+    return out
+
+
+def shell_flops_per_node(S):
+    """Flops of one output of the shell kernel: per +-e pair two differences and, per nonzero
+    component of e, one multiply-add (2 flops) into each of the two sums; plus the epilogue."""
+    f = 0
+    for e in half_shell(S):
+        f += 2 + 4 * sum(1 for v in e if v != 0)
+    return f + 3 * 4 + 2
+
+
+def source_hash(files):
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+KERNEL_SOURCES = {
+    "collide": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "shell": ["paper_1202_3842_gb300/csrc/lbe_shell.cu", "paper_1202_3842_gb300/csrc/lbe_shell.cuh",
+              "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "contact": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "flux": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu"],
+}
+
+
+def traffic_for(stage, workload, prec):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel source is unchanged."""
+    try:
+        T = json.load(open(TRAFFIC_FILE))
+        e = T[stage][workload][prec]
+        if e.get("source_hash") != source_hash(KERNEL_SOURCES[stage]):
+            return None
+        return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle leg
+# ---------------------------------------------------------------------------
+def oracle_sample_sim(w, arrays, L):
+    import numpy as np
+    import oracle
+    shape = w["shape"]
+    cx, cy, cz = (s // 2 for s in shape)
+
+    def sub(field):
+        f = field.reshape(shape[2], shape[1], shape[0])
+        xs = [(cx + d) % shape[0] for d in range(-L // 2, L - L // 2)]
+        ys = [(cy + d) % shape[1] for d in range(-L // 2, L - L // 2)]
+        zs = [(cz + d) % shape[2] for d in range(-L // 2, L - L // 2)]
+        return f[np.ix_(zs, ys, xs)].reshape(-1)
+
+    M = len(w["sigma"])
+    sim = oracle.Sim((L, L, L), (1, 1, 1), M)
+    for a in range(M):
+        sim.set_species(a, w["sigma"][a], w["tau"][a])
+        sim.set_potential(a, sub(arrays["V"][a]))
+        sim.set_body_force(a, w["body"][a])
+    for a in range(M):
+        sim.init_density(a, sub(arrays["n"][a]))
+    return sim
+
+
+def cpu_baseline(w, arrays, L=32, min_s=10.0, max_steps=400):
+    sim = oracle_sample_sim(w, arrays, L)
+    M = len(w["sigma"])
+    sim.step(1)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_steps:
+        sim.step(1)
+        n += 1
+        if time.perf_counter() - t0 >= min_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": L ** 3 * M * n / dt / 1e6, "unit": "MLUPS/species", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of a %d^3 periodic sub-box cut from the centre of the %s workload (same sigma, "
+                      "packing, tau, potential), single-threaded FP64 C oracle" % (n, L, w.get("name", "?"))}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1202_3842_gb300 import inputs
+    w = inputs.WORKLOADS[args.workload]()
+    w["name"] = args.workload
+    arrays = inputs.build_workload(w)
+    L = 24
+    sim = oracle_sample_sim(w, arrays, L)
+    M = len(w["sigma"])
+    for _ in range(args.warmup):
+        sim.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.step(1)
+    dt = time.perf_counter() - t0
+    value = L ** 3 * M * args.steps / dt / 1e6
+    sample = ("each step is one FP64 oracle step of a %d^3 periodic sub-box cut from the centre of the %s workload"
+              % (L, args.workload))
+    line = {"impl": "reference", "metric": "Enskog-LB MLUPS/species", "value": value, "unit": "MLUPS/species",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + WORKLOAD_TEXT.get(args.workload, ""), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS/species", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MLUPS/species", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------
+def make_sim(w, arrays, prec):
+    from paper_1202_3842_gb300 import lbe
+    M = len(w["sigma"])
+    sim = lbe.Simulation(w["shape"], w["periodic"], M, prec)
+    if arrays["solid"].any():
+        sim.set_geometry(arrays["solid"])
+    for a in range(M):
+        sim.set_species(a, w["sigma"][a], w["tau"][a])
+        sim.set_potential(a, arrays["V"][a])
+        sim.set_body_force(a, w["body"][a])
+    if arrays["amp"].any():
+        sim.set_wall_potential(arrays["phi"], arrays["amp"])
+    for a in range(M):
+        sim.init_density(a, arrays["n"][a])
+    if w["kind"] == "channel":
+        sim.set_flux_plane(0, w["shape"][0] // 2)
+    return sim
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1202_3842_gb300 import build, inputs, lbe
+    build.build()
+    w = inputs.WORKLOADS[args.workload]()
+    w["name"] = args.workload
+    arrays = inputs.build_workload(w)
+    M = len(w["sigma"])
+    nx, ny, nz = w["shape"]
+    N = nx * ny * nz
+    peaks, peaks_kind = load_peaks()
+
+    sim = make_sim(w, arrays, args.prec)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.5)
+    sim.set_stage_timing(True)
+    l0 = sim.launch_count()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.mark("t0")
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.mark("t1")
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count() - l0
+    stages = sim.stage_times()
+    sim.set_stage_timing(False)
+    clocks = sampler.stop()
+    m_after, _, umax = sim.totals()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    ms_step = ms / args.steps
+    value = world * N * M * args.steps / (ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel (largest share of the timed device time)
+    dom = max(stages, key=lambda k: stages[k][0])
+    dom_ms, dom_n = stages[dom]
+    per_launch_ms = dom_ms / max(dom_n, 1)
+    sb = STORE_BYTES[args.prec]
+    if dom == "collide":
+        alg = N * M * 4 * QPOP * sb  # populations f~ and g~ read + written
+        achieved = alg / (per_launch_ms * 1e-3) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"kernel": "k_collide (K4 fused moments + DD-TR collision + streaming)", "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic_for("collide", args.workload, args.prec), "algorithmic_bytes_per_launch": alg,
+                "peak_source": peaks_kind + " hbm_gbs (STREAM-style copy)"}
+    else:
+        S_list = []
+        for a in range(M):
+            for b in range(M):
+                S_list.append(int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))))
+        flops = sum(shell_flops_per_node(S) for S in S_list) * N
+        per_launch_flops = flops / len(S_list)
+        achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
+        clk = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12 if args.prec != "fp64" else None
+        roof = {"kernel": "k_shell_force (K3 mean-field shell force)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "traffic": traffic_for("shell", args.workload, args.prec),
+                "algorithmic_flops_per_launch": per_launch_flops,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % clk}
+    # whole-step population bandwidth (context)
+    step_bytes = N * M * 4 * QPOP * sb
+    result = {
+        "metric": "Enskog-LB MLUPS/species", "value": value, "unit": "MLUPS/species", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
+        "data": "synthetic (seeded inputs of the workload's shape and distribution)",
+        "config": {"workload": args.workload + ": " + WORKLOAD_TEXT.get(args.workload, ""),
+                   "precision": args.prec, "nodes": N, "species": M,
+                   "l2": "inputs larger than L2: population buffers %.2f GB each" % (N * M * 2 * QPOP * sb / 1e9),
+                   "parallelism": "replicas only (one independent lattice per GPU)" if world > 1 else "1 GPU"},
+        "roofline": roof,
+        "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "population_gbs_whole_step": step_bytes / (ms_step * 1e-3) / 1e9,
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "max_u_over_vT_after": umax / math.sqrt(1.0 / 3.0),
+    }
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI with host buffers: the timed region holds the host->device copy of the
+    # initial densities (pinned), the steps and the device->host read of the final densities
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(arrays["n"][a].copy()).pin_memory() for a in range(M)]
+        out = torch.empty(N, dtype=torch.float64).pin_memory()
+        sim = make_sim(w, arrays, args.prec)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for a in range(M):
+            lbe.lbe_init_density(sim._h, N, a, pinned[a].numpy())
+        sim.step(args.steps)
+        res = 0.0
+        for a in range(M):
+            lbe.lbe_get_density(sim._h, N, a, out.numpy())
+            res += float(out[0])
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([t_e2e], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        result["e2e"] = {"value": world * N * M * args.steps / t_e2e / 1e6, "unit": "MLUPS/species",
+                         "h2d_bytes_per_step": 8 * N * M / args.steps, "d2h_bytes_per_step": 8 * N * M / args.steps,
+                         "what": "lbe_init_density from pinned host FP64 + %d x lbe_step + lbe_get_density to "
+                                 "pinned host, wall clock" % args.steps}
+        sim.close()
+        del sim
+
+    if rank == 0 and not args.no_cpu:
+        result["cpu_baseline"] = cpu_baseline(w, arrays)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -189,6 +189,23 @@ lbe_status lbe_get_link_mask(lbe_ctx *ctx, uint32_t *out);
  * as [k][3] ints into e (may be NULL) and the count into *count. */
 lbe_status lbe_shell(double sigma, int *e, int cap, int *count);
 
+/* Stage timing: CUDA events recorded on the context stream around every kernel
+ * launch of lbe_step.  on != 0 enables it and clears the totals; 0 disables it. */
+lbe_status lbe_set_stage_timing(lbe_ctx *ctx, int on);
+
+/* Stages of one step, in launch order. */
+#define LBE_NUM_STAGES 5
+enum { LBE_STAGE_DENSITY = 0,  /* K1: pulled zeroth moment into the padded field */
+       LBE_STAGE_CONTACT = 1,  /* K2: ball averages and contact values         */
+       LBE_STAGE_SHELL = 2,    /* K3: mean-field shell force, one launch per pair */
+       LBE_STAGE_COLLIDE = 3,  /* K4: moments + DD-TR collision + streaming     */
+       LBE_STAGE_FLUX = 4 };   /* K5: plane flux reduction                      */
+
+/* Device time in milliseconds ms[LBE_NUM_STAGES] and launch counts
+ * launches[LBE_NUM_STAGES] accumulated since timing was enabled (synchronises;
+ * either pointer may be NULL). */
+lbe_status lbe_get_stage_times(lbe_ctx *ctx, double *ms, long long *launches);
+
 /* Number of kernel launches this context has issued (all entry points). */
 lbe_status lbe_get_launch_count(lbe_ctx *ctx, long long *launches);
 

@@ -74,6 +74,13 @@ struct lbe_ctx {
     long long launches = 0;
     long long steps_since_check = 0;
     std::string last_error;
+
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending[LBE_NUM_STAGES];
+    double stage_ms[LBE_NUM_STAGES] = {0};
+    long long stage_launches[LBE_NUM_STAGES] = {0};
 };
 
 namespace {
@@ -147,6 +154,52 @@ void dev_free(lbe_ctx *c, Buf &b) {
     } while (0)
 
 size_t real_bytes(const lbe_ctx *c) { return prec_fp64(c->prec) ? 8 : 4; }
+
+cudaEvent_t pool_event(lbe_ctx *c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets one kernel launch of a stage with events when timing is on.
+struct StageTimer {
+    lbe_ctx *c;
+    int stage;
+    cudaEvent_t a = nullptr, b = nullptr;
+    StageTimer(lbe_ctx *c_, int st) : c(c_), stage(st) {
+        if (c->timing) {
+            a = pool_event(c);
+            b = pool_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~StageTimer() {
+        if (c->timing && a && b) {
+            cudaEventRecord(b, c->stream);
+            c->ev_pending[stage].push_back({a, b});
+            c->stage_launches[stage] += 1;
+        }
+    }
+};
+
+// Fold the pending event pairs into the totals (synchronises the stream).
+void fold_stage_times(lbe_ctx *c) {
+    cudaStreamSynchronize(c->stream);
+    for (int s = 0; s < LBE_NUM_STAGES; ++s) {
+        for (auto &pr : c->ev_pending[s]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) c->stage_ms[s] += ms;
+            c->ev_pool.push_back(pr.first);
+            c->ev_pool.push_back(pr.second);
+        }
+        c->ev_pending[s].clear();
+    }
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -314,13 +367,19 @@ StepParams step_params(const lbe_ctx *c) {
 lbe_status force_stage(lbe_ctx *c) {
     const bool f64 = prec_fp64(c->prec);
     const size_t rb = real_bytes(c);
-    LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->M, c->n0, c->npad.p,
-                          (int *)c->err.p, c->stream),
-           "density kernel");
+    {
+        StageTimer t(c, LBE_STAGE_DENSITY);
+        LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->M, c->n0, c->npad.p,
+                              (int *)c->err.p, c->stream),
+               "density kernel");
+    }
     if (c->pairs.empty()) return LBE_OK;  // ideal gas: C stays zero
-    LAUNCH(launch_contact(f64, c->g, c->cparams, (const int *)c->ball.p, c->npad.p, c->gab.p, c->gnpad.p,
-                          (int *)c->err.p, c->stream),
-           "contact kernel");
+    {
+        StageTimer t(c, LBE_STAGE_CONTACT);
+        LAUNCH(launch_contact(f64, c->g, c->cparams, (const int *)c->ball.p, c->npad.p, c->gab.p, c->gnpad.p,
+                              (int *)c->err.p, c->stream),
+               "contact kernel");
+    }
     std::vector<int> first(c->M, 1);
     for (auto &ps : c->pairs) {
         ShellLaunch L{};
@@ -334,6 +393,7 @@ lbe_status force_stage(lbe_ctx *c) {
         L.accumulate = first[ps.a] ? 0 : 1;
         L.err = (int *)c->err.p;
         first[ps.a] = 0;
+        StageTimer t(c, LBE_STAGE_SHELL);
         LAUNCH(launch_shell_force(f64, ps.S, L, c->stream), "shell force kernel");
     }
     for (int a = 0; a < c->M; ++a)
@@ -486,6 +546,9 @@ void lbe_destroy(lbe_ctx *c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
+    fold_stage_times(c);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    c->ev_pool.clear();
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->ball, &c->flux_buf, &c->flux_acc,
                   &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out};
@@ -594,11 +657,16 @@ lbe_status lbe_step(lbe_ctx *c, int nsteps) {
     if (psize > 0) TRY(dev_alloc(c, c->flux_buf, 8 * (size_t)c->M * psize));
     for (int t = 0; t < nsteps; ++t) {
         TRY(force_stage(c));
-        LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
-                              c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
-               "collide kernel");
+        {
+            StageTimer tm(c, LBE_STAGE_COLLIDE);
+            LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p,
+                                  (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, (double *)c->flux_buf.p,
+                                  c->stream),
+                   "collide kernel");
+        }
         c->cur = 1 - c->cur;
         if (psize > 0) {
+            StageTimer tm(c, LBE_STAGE_FLUX);
             LAUNCH(launch_flux_reduce(c->M, psize, (const double *)c->flux_buf.p, (double *)c->flux_acc.p,
                                       (double *)c->flux_last.p, c->stream),
                    "flux reduction");
@@ -838,6 +906,27 @@ lbe_status lbe_shell(double sigma, int *e, int cap, int *count) {
                     ++k;
                 }
     *count = k;
+    return LBE_OK;
+}
+
+lbe_status lbe_set_stage_timing(lbe_ctx *c, int on) {
+    TRY(ready(c));
+    fold_stage_times(c);
+    c->timing = on != 0;
+    for (int s = 0; s < LBE_NUM_STAGES; ++s) {
+        c->stage_ms[s] = 0.0;
+        c->stage_launches[s] = 0;
+    }
+    return LBE_OK;
+}
+
+lbe_status lbe_get_stage_times(lbe_ctx *c, double *ms, long long *launches) {
+    TRY(ready(c));
+    fold_stage_times(c);
+    for (int s = 0; s < LBE_NUM_STAGES; ++s) {
+        if (ms) ms[s] = c->stage_ms[s];
+        if (launches) launches[s] = c->stage_launches[s];
+    }
     return LBE_OK;
 }
 

@@ -45,6 +45,8 @@ enum : int {
 // Population storage.  S is the stored type, T the arithmetic type.  The
 // 16-bit forms hold s = f/(w n0) - 1 (populations shifted by their rest value
 // and normalised), so the small deviations keep their relative precision.
+// load() takes wn0 = w_p n0, store() takes its reciprocal 1/(w_p n0) (both
+// unused by the unshifted forms).
 // ---------------------------------------------------------------------------
 template <typename S, typename T>
 struct Store;
@@ -67,8 +69,9 @@ struct Store<__nv_bfloat16, float> {
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p, float wn0) {
         return fmaf(wn0, __bfloat162float(__ldg(p)), wn0);
     }
-    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, float wn0) {
-        *p = __float2bfloat16_rn(v / wn0 - 1.0f);
+    // iwn0 = 1/(w_p n0)
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, float iwn0) {
+        *p = __float2bfloat16_rn(fmaf(v, iwn0, -1.0f));
     }
     static constexpr bool shifted = true;
 };
@@ -77,8 +80,8 @@ struct Store<__half, float> {
     static __device__ __forceinline__ float load(const __half *p, float wn0) {
         return fmaf(wn0, __half2float(__ldg(p)), wn0);
     }
-    static __device__ __forceinline__ void store(__half *p, float v, float wn0) {
-        *p = __float2half_rn(v / wn0 - 1.0f);
+    static __device__ __forceinline__ void store(__half *p, float v, float iwn0) {
+        *p = __float2half_rn(fmaf(v, iwn0, -1.0f));
     }
     static constexpr bool shifted = true;
 };

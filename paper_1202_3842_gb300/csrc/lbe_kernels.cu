@@ -154,9 +154,9 @@ __global__ void k_unstream(Grid g, const uint32_t *__restrict__ mask, const doub
                 gv = gq[(long long)opp(p) * g.N + s];
             }
         }
-        const T wn0 = (T)wq(p) * n0;
-        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)fv, wn0);
-        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)gv, wn0);
+        const T iwn0 = (T)1 / ((T)wq(p) * n0);
+        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)fv, iwn0);
+        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)gv, iwn0);
     }
 }
 
@@ -178,9 +178,9 @@ __global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const do
             long long t = ok ? X + (long long)g.nx * (Y + (long long)g.ny * Z) : 0;
             v = (ok && !(mask[t] & 1u)) ? wq(p) * n[t] : wq(p) * n[s];
         }
-        const T wn0 = (T)wq(p) * n0;
-        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)v, wn0);
-        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)v, wn0);
+        const T iwn0 = (T)1 / ((T)wq(p) * n0);
+        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)v, iwn0);
+        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)v, iwn0);
     }
 }
 
@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
         const T sf0 = (T)-3 * (X[0] * ua[0] + X[1] * ua[1] + X[2] * ua[2]);
         const T om = (T)sp.sp[a].omega_eff;
         const T inv = (T)sp.sp[a].inv;
-        const T n0 = (T)sp.sp[a].n0;
+        const T in0 = sp.sp[a].n0 > 0.0 ? (T)(1.0 / sp.sp[a].n0) : (T)0;
         S *fo = dst + pop_off(a, 0, 0, g.N) + i;
         S *go = dst + pop_off(a, 1, 0, g.N) + i;
         [&]<int... P>(std::integer_sequence<int, P...>) {
@@ -475,8 +475,9 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
                     const T Sg = w * (sf0 + (T)3 * cY + (T)18 * cC * cua + (T)9 * cY * cua);
                     const T fs = st.f[a][P] + om * (feq - st.f[a][P]) + inv * Sf;
                     const T gs = st.g[a][P] + om * (geq - st.g[a][P]) + inv * Sg;
-                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * n0);
-                    Store<S, T>::store(go + (long long)P * g.N, gs, w * n0);
+                    constexpr T iw = (T)(1.0 / wq(P));
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, iw * in0);
+                    Store<S, T>::store(go + (long long)P * g.N, gs, iw * in0);
                 }(),
                 ...);
         }(std::make_integer_sequence<int, Q>{});

@@ -72,7 +72,7 @@ struct ShellTile {
     static constexpr int PLANE = BX * BY;  // elements of one field plane
     static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;  // density plane + g*n plane
-    static constexpr int SMEM = R * SLOT_BYTES + 128 /*barriers*/ + 128 /*alignment*/;
+    static constexpr int SMEM = R * SLOT_BYTES + 256 /*barriers*/ + 128 /*alignment*/;
     static constexpr int LZ = 32;
 };
 

@@ -185,6 +185,8 @@ WORKLOADS = {
     "well24": lambda: well_workload((24, 24, 24), 3.0, 0.2, 1.0, 1.0, 5.0),
     # one-component spherical well at production size: 256^3, sigma = 6, eta = 0.3, 2 kT / R = 24, tau = 0.8
     "well256": lambda: well_workload((256, 256, 256), 6.0, 0.3, 0.8, 2.0, 24.0),
+    # same well at 160^3 (radius scaled to 15): the small case of the profiler captures
+    "well160": lambda: well_workload((160, 160, 160), 6.0, 0.3, 0.8, 2.0, 15.0),
     # two-component bottleneck channel 512x128x128, sigma 4/6, eta 0.25, width 16, length 64, g = 1e-6
     "channel512": lambda: channel_workload((512, 128, 128), (4.0, 6.0), 0.25, (1.0, 1.0), 16, 64),
     # same channel at 128x32x32 (same absolute width and diameters)

@@ -82,6 +82,8 @@ def lib():
             "lbe_get_link_mask": [_P, ctypes.POINTER(ctypes.c_uint32)],
             "lbe_shell": [ctypes.c_double, _I, ctypes.c_int, _I],
             "lbe_get_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+            "lbe_set_stage_timing": [_P, ctypes.c_int],
+            "lbe_get_stage_times": [_P, _D, ctypes.POINTER(ctypes.c_longlong)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -308,6 +310,20 @@ def lbe_get_launch_count(ctx):
     return v.value
 
 
+STAGES = ("density", "contact", "shell", "collide", "flux")
+
+
+def lbe_set_stage_timing(ctx, on):
+    _check(lib().lbe_set_stage_timing(ctx, int(bool(on))), ctx)
+
+
+def lbe_get_stage_times(ctx):
+    ms = np.zeros(5)
+    n = (ctypes.c_longlong * 5)()
+    _check(lib().lbe_get_stage_times(ctx, _dp(ms), n), ctx)
+    return {STAGES[k]: (float(ms[k]), int(n[k])) for k in range(5)}
+
+
 def lbe_status_string(status):
     return lib().lbe_status_string(int(status)).decode()
 
@@ -409,3 +425,10 @@ class Simulation:
 
     def launch_count(self):
         return lbe_get_launch_count(self._h)
+
+    def set_stage_timing(self, on):
+        lbe_set_stage_timing(self._h, on)
+
+    def stage_times(self):
+        """{stage: (device ms, launches)} since timing was enabled."""
+        return lbe_get_stage_times(self._h)
