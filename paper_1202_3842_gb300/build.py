@@ -40,6 +40,8 @@ def _compile(src, extra):
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))
+    if extra:
+        sys.stderr.write(r.stderr)
     return obj
 
 

@@ -56,7 +56,7 @@ struct lbe_ctx {
     Buf pop[2];
     int cur = 0;
     Buf solid, mask, V, phi, amp, F;
-    Buf npad, gab, gnpad, C, ball;
+    Buf npad, gab, gnpad, C;
     Buf flux_buf, flux_acc, flux_last;
     Buf err;
     Buf scratch64;  // FP64 scratch for getters: n [M][N] + J [M][3][N] (+ more)
@@ -66,6 +66,10 @@ struct lbe_ctx {
     bool geom_dirty = true, force_dirty = true, fields_dirty = true;
     std::vector<PairShell> pairs;
     ContactParams cparams{};
+    BallRows brows{};
+    int RB = 0;
+    CUtensorMap contact_maps[MAXS];
+    bool solid_links = false;  // some link can be blocked: a solid node or a closed axis
     int H = 0;
 
     long long steps = 0;
@@ -214,12 +218,10 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-lbe_status make_map(lbe_ctx *c, CUtensorMap *map, void *base, int S) {
+lbe_status make_map(lbe_ctx *c, CUtensorMap *map, void *base, int bx, int by) {
     auto enc = get_encode();
     if (!enc) return fail(c, LBE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const bool f64 = prec_fp64(c->prec);
-    int bx = 0, by = 0;
-    shell_box(f64, S, &bx, &by);
     const size_t es = f64 ? 8 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)c->g.px, (cuuint64_t)c->g.py, (cuuint64_t)c->g.pz};
     cuuint64_t strides[2] = {(cuuint64_t)c->g.px * es, (cuuint64_t)c->g.px * c->g.py * es};
@@ -280,17 +282,20 @@ lbe_status prepare(lbe_ctx *c) {
                 H = std::max(H, S);
             }
         // ball radii
-        std::vector<int> ball;
         ContactParams cp{};
         cp.M = c->M;
+        int RB = 0;
         for (int b = 0; b < c->M; ++b) {
             double R = 0.5 * c->sigma[b];
             int Ri = (int)std::floor(R);
-            H = std::max(H, Ri);
+            RB = std::max(RB, Ri);
             cp.sigma[b] = c->sigma[b];
             cp.xi2c[b] = kPi / 6.0 * c->sigma[b] * c->sigma[b];
             cp.xi3c[b] = kPi / 6.0 * c->sigma[b] * c->sigma[b] * c->sigma[b];
         }
+        if (RB > 4) return fail(c, LBE_ERR_UNSUPPORTED, "ball radius sigma/2 above 4 lattice units");
+        H = std::max(H, RB);
+        c->RB = RB;
         c->H = H;
         Grid &g = c->g;
         g.H = H;
@@ -298,17 +303,28 @@ lbe_status prepare(lbe_ctx *c) {
         g.py = g.ny + 2 * H;
         g.pz = g.nz + 2 * H;
         g.P = (long long)g.px * g.py * g.pz;
+        // averaging ball |d| <= sigma_b/2 as rows (dy, dz) of half-width a along x
+        BallRows br{};
         for (int b = 0; b < c->M; ++b) {
-            double R = 0.5 * c->sigma[b];
-            int Ri = (int)std::floor(R);
-            cp.ball_start[b] = (int)ball.size();
-            for (int z = -Ri; z <= Ri; ++z)
-                for (int y = -Ri; y <= Ri; ++y)
-                    for (int x = -Ri; x <= Ri; ++x)
-                        if ((double)(x * x + y * y + z * z) <= R * R)
-                            ball.push_back(x + g.px * (y + g.py * z));
-            cp.ball_count[b] = (int)ball.size() - cp.ball_start[b];
+            const double R = 0.5 * c->sigma[b], R2 = R * R;
+            const int Ri = (int)std::floor(R);
+            int nr = 0, cnt = 0;
+            for (int dz = -Ri; dz <= Ri; ++dz)
+                for (int dy = -Ri; dy <= Ri; ++dy) {
+                    const double rem = R2 - (double)(dy * dy + dz * dz);
+                    if (rem < 0.0) continue;
+                    int a = 0;
+                    while ((double)((a + 1) * (a + 1)) <= rem) ++a;
+                    br.dy[b][nr] = (signed char)dy;
+                    br.dz[b][nr] = (signed char)dz;
+                    br.a[b][nr] = (signed char)a;
+                    cnt += 2 * a + 1;
+                    ++nr;
+                }
+            br.nrows[b] = nr;
+            br.count[b] = cnt;
         }
+        c->brows = br;
         for (int a = 0; a < c->M; ++a)
             for (int b = 0; b < c->M; ++b) {
                 double sa = c->sigma[a], sb = c->sigma[b];
@@ -320,17 +336,22 @@ lbe_status prepare(lbe_ctx *c) {
         TRY(dev_alloc(c, c->gnpad, rb * c->M * c->M * g.P));
         TRY(dev_alloc(c, c->gab, rb * c->M * c->M * g.N));
         TRY(dev_alloc(c, c->C, rb * c->M * 3 * g.N));
-        TRY(dev_alloc(c, c->ball, sizeof(int) * ball.size()));
         CK(cudaMemsetAsync(c->npad.p, 0, rb * c->M * g.P, c->stream), "memset npad");
         CK(cudaMemsetAsync(c->gnpad.p, 0, rb * c->M * c->M * g.P, c->stream), "memset gnpad");
         CK(cudaMemsetAsync(c->C.p, 0, rb * c->M * 3 * g.N, c->stream), "memset C");
-        CK(cudaMemcpyAsync(c->ball.p, ball.data(), sizeof(int) * ball.size(), cudaMemcpyHostToDevice, c->stream),
-           "copy ball table");
         for (auto &ps : c->pairs) {
             char *nb = (char *)c->npad.p + rb * ps.b * g.P;
             char *gn = (char *)c->gnpad.p + rb * (ps.a * c->M + ps.b) * g.P;
-            TRY(make_map(c, &ps.map_n, nb, ps.S));
-            TRY(make_map(c, &ps.map_gn, gn, ps.S));
+            int bx = 0, by = 0;
+            shell_box(f64, ps.S, &bx, &by);
+            TRY(make_map(c, &ps.map_n, nb, bx, by));
+            TRY(make_map(c, &ps.map_gn, gn, bx, by));
+        }
+        {
+            int bx = 0, by = 0;
+            contact_box(f64, c->M, c->RB, &bx, &by);
+            for (int b = 0; b < c->M; ++b)
+                TRY(make_map(c, &c->contact_maps[b], (char *)c->npad.p + rb * b * g.P, bx, by));
         }
         c->fields_dirty = false;
     }
@@ -369,16 +390,23 @@ lbe_status force_stage(lbe_ctx *c) {
     const size_t rb = real_bytes(c);
     {
         StageTimer t(c, LBE_STAGE_DENSITY);
-        LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->M, c->n0, c->npad.p,
-                              (int *)c->err.p, c->stream),
+            LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->solid_links, c->M,
+                              c->n0, c->npad.p, (int *)c->err.p, c->stream),
                "density kernel");
     }
     if (c->pairs.empty()) return LBE_OK;  // ideal gas: C stays zero
     {
         StageTimer t(c, LBE_STAGE_CONTACT);
-        LAUNCH(launch_contact(f64, c->g, c->cparams, (const int *)c->ball.p, c->npad.p, c->gab.p, c->gnpad.p,
-                              (int *)c->err.p, c->stream),
-               "contact kernel");
+        ContactLaunch L{};
+        L.grid = &c->g;
+        L.maps = c->contact_maps;
+        L.cp = &c->cparams;
+        L.br = &c->brows;
+        L.RB = c->RB;
+        L.gab = c->gab.p;
+        L.gnpad = c->gnpad.p;
+        L.err = (int *)c->err.p;
+        LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
     }
     std::vector<int> first(c->M, 1);
     for (auto &ps : c->pairs) {
@@ -530,6 +558,7 @@ lbe_status lbe_create(const lbe_config *cfg, const lbe_allocator *allocator, voi
     cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream);
     cudaMemsetAsync(c->flux_last.p, 0, 8 * MAXS, c->stream);
     c->solid_h.assign(g.N, 0);
+    c->solid_links = !(g.per[0] && g.per[1] && g.per[2]);
     e = launch_link_mask(g, (const uint8_t *)c->solid.p, (uint32_t *)c->mask.p, c->stream);
     c->launches += 1;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -550,7 +579,7 @@ void lbe_destroy(lbe_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
-                  &c->npad, &c->gab, &c->gnpad, &c->C, &c->ball, &c->flux_buf, &c->flux_acc,
+                  &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
                   &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out};
     for (Buf *b : all) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
@@ -561,7 +590,12 @@ lbe_status lbe_set_geometry(lbe_ctx *c, const uint8_t *solid) {
     TRY(ready(c));
     if (!solid) return fail(c, LBE_ERR_INVALID_ARG, "null solid mask");
     const long long N = c->g.N;
-    for (long long i = 0; i < N; ++i) c->solid_h[i] = solid[i] ? 1 : 0;
+    bool any = false;
+    for (long long i = 0; i < N; ++i) {
+        c->solid_h[i] = solid[i] ? 1 : 0;
+        any = any || solid[i];
+    }
+    c->solid_links = any || !(c->g.per[0] && c->g.per[1] && c->g.per[2]);
     CK(cudaMemcpyAsync(c->solid.p, c->solid_h.data(), N, cudaMemcpyHostToDevice, c->stream), "copy solid");
     LAUNCH(launch_link_mask(c->g, (const uint8_t *)c->solid.p, (uint32_t *)c->mask.p, c->stream), "link mask");
     CK(cudaStreamSynchronize(c->stream), "stream sync");
@@ -660,8 +694,8 @@ lbe_status lbe_step(lbe_ctx *c, int nsteps) {
         {
             StageTimer tm(c, LBE_STAGE_COLLIDE);
             LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p,
-                                  (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, (double *)c->flux_buf.p,
-                                  c->stream),
+                                  (const uint32_t *)c->mask.p, c->solid_links, c->C.p, c->F.p, sp,
+                                  (double *)c->flux_buf.p, c->stream),
                    "collide kernel");
         }
         c->cur = 1 - c->cur;

@@ -184,13 +184,17 @@ __global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const do
     }
 }
 
-template <typename S, typename T, int P>
+template <typename S, typename T, int P, bool SOLID = true>
 __device__ __forceinline__ T pull(const S *__restrict__ fg_base, long long N, long long i, const NbrOff &o,
                                   uint32_t m, T n0) {
     // fg_base points at population 0 of this species' f (or g) block
     const T wn0 = (T)wq(P) * n0;
-    if (m & (1u << P)) return Store<S, T>::load(fg_base + (long long)opp(P) * N + i, wn0);
-    return Store<S, T>::load(fg_base + (long long)P * N + i + src_off<P>(o), wn0);
+    if constexpr (SOLID) {
+        const long long off = (m & (1u << P)) ? (long long)opp(P) * N + i : (long long)P * N + i + src_off<P>(o);
+        return Store<S, T>::load(fg_base + off, wn0);
+    } else {
+        return Store<S, T>::load(fg_base + (long long)P * N + i + src_off<P>(o), wn0);
+    }
 }
 
 template <typename S, typename T>
@@ -259,14 +263,14 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
     int x, y, z;
     node_xyz(g, i, x, y, z);
     const uint32_t m = SOLID ? mask[i] : 0u;
-    const NbrOff o = nbr_offsets(g, x, y, z);
+    const NbrOff o = nbr_offsets(g, x, y, z);  // (without solids every axis is periodic)
     for (int a = 0; a < M; ++a) {
         T n = (T)0;
         if (!(m & 1u)) {
             const S *fb = pop + pop_off(a, 0, 0, g.N);
             const T n0 = (T)n0v.v[a];
             [&]<int... P>(std::integer_sequence<int, P...>) {
-                ((n += pull<S, T, P>(fb, g.N, i, o, m, n0)), ...);
+                ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
             }(std::make_integer_sequence<int, Q>{});
             if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
         }
@@ -274,62 +278,16 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
     }
 }
 
-cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, int M,
+cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
                            const double *n0, void *npad, int *err, cudaStream_t st) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
     N0Vec n0v;
     for (int a = 0; a < MAXS; ++a) n0v.v[a] = a < M ? n0[a] : 0.0;
-    LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
-    return cudaGetLastError();
-}
-
-// ---------------------------------------------------------------------------
-// K2: contact values.  n-bar_b = mean of n_b over the ball |d| <= sigma_b/2,
-// xi_k = (pi/6) sum_b sigma_b^k n-bar_b, and the Boublik-Mansoori-Carnahan-
-// Starling-Leland contact value g_ab = 1/(1-xi3) + 3 s xi2/(1-xi3)^2
-// + 2 s^2 xi2^2/(1-xi3)^3 with s = sigma_a sigma_b/(sigma_a + sigma_b).
-// Writes g_ab [M][M][N] and the padded product g_ab * n_b [M][M][P].
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(NT) k_contact(Grid g, ContactParams cp, const int *__restrict__ ball,
-                                                const T *__restrict__ npad, T *__restrict__ gab,
-                                                T *__restrict__ gnpad, int *err) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
-    int x, y, z;
-    node_xyz(g, i, x, y, z);
-    const long long pc = pidx(g, x, y, z);
-    T xi2 = 0, xi3 = 0;
-    T nloc[MAXS];
-    for (int b = 0; b < cp.M; ++b) {
-        const T *nb = npad + (long long)b * g.P + pc;
-        const int k0 = cp.ball_start[b], k1 = k0 + cp.ball_count[b];
-        T acc = 0;
-        for (int k = k0; k < k1; ++k) acc += __ldg(nb + __ldg(ball + k));
-        const T nbar = acc / (T)cp.ball_count[b];
-        xi2 += (T)cp.xi2c[b] * nbar;
-        xi3 += (T)cp.xi3c[b] * nbar;
-        nloc[b] = nb[0];
+    if (solid) {
+        LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
+    } else {
+        LBE_DISPATCH_PREC(p, (k_density<S, T, false><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
     }
-    const T i1 = (T)1 / ((T)1 - xi3);
-    if (!(xi3 < (T)1)) atomicOr(err, ERR_PACKING);
-    for (int a = 0; a < cp.M; ++a)
-        for (int b = 0; b < cp.M; ++b) {
-            const T s = (T)cp.s_ab[a][b];
-            const T gv = i1 + (T)3 * s * xi2 * i1 * i1 + (T)2 * s * s * xi2 * xi2 * i1 * i1 * i1;
-            if (!isfinite(gv)) atomicOr(err, ERR_PACKING);
-            gab[(long long)(a * cp.M + b) * g.N + i] = gv;
-            write_padded<T>(g, gnpad + (long long)(a * cp.M + b) * g.P, x, y, z, gv * nloc[b]);
-        }
-}
-
-cudaError_t launch_contact(bool fp64, const Grid &g, const ContactParams &cp, const int *ball, const void *npad,
-                           void *gab, void *gnpad, int *err, cudaStream_t st) {
-    unsigned nb = (unsigned)((g.N + NT - 1) / NT);
-    if (fp64)
-        k_contact<double><<<nb, NT, 0, st>>>(g, cp, ball, (const double *)npad, (double *)gab, (double *)gnpad, err);
-    else
-        k_contact<float><<<nb, NT, 0, st>>>(g, cp, ball, (const float *)npad, (float *)gab, (float *)gnpad, err);
     return cudaGetLastError();
 }
 
@@ -359,34 +317,46 @@ __device__ __forceinline__ T cdot(const T *v) {
     return r;
 }
 
-template <typename S, typename T, int M>
+// Per-node moments of every species.  With KEEP the pulled populations stay
+// in registers for the collision (one species); otherwise they are pulled
+// again species by species in the collision pass (the second pull hits L2).
+template <typename S, typename T, int M, bool KEEP>
 struct NodeState {
-    T f[M][Q], g[M][Q];
+    T f[KEEP ? M : 1][Q], g[KEEP ? M : 1][Q];
     T n[M], Pi[M], J[M][3], C[M][3], nF[M][3], ua[M][3];
     T u[3];
 };
 
-template <typename S, typename T, int M>
+template <typename S, typename T, bool SOLID>
+__device__ __forceinline__ void pull_species(const Grid &g, const S *__restrict__ src, int a, T n0, long long i,
+                                             const NbrOff &o, uint32_t m, T *f, T *gq) {
+    const S *fb = src + pop_off(a, 0, 0, g.N);
+    const S *gb = src + pop_off(a, 1, 0, g.N);
+    [&]<int... P>(std::integer_sequence<int, P...>) {
+        ((f[P] = pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+        ((gq[P] = pull<S, T, P, SOLID>(gb, g.N, i, o, m, n0)), ...);
+    }(std::make_integer_sequence<int, Q>{});
+}
+
+template <typename S, typename T, int M, bool SOLID, bool KEEP>
 __device__ __forceinline__ void load_moments(const Grid &g, const S *__restrict__ src, const T *__restrict__ C,
                                              const T *__restrict__ F, const StepParams &sp, long long i,
-                                             const NbrOff &o, uint32_t m, NodeState<S, T, M> &st) {
+                                             const NbrOff &o, uint32_t m, NodeState<S, T, M, KEEP> &st) {
     T ntot = 0, Jtot[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < M; ++a) {
         const T n0 = (T)sp.sp[a].n0;
-        const S *fb = src + pop_off(a, 0, 0, g.N);
-        const S *gb = src + pop_off(a, 1, 0, g.N);
-        [&]<int... P>(std::integer_sequence<int, P...>) {
-            ((st.f[a][P] = pull<S, T, P>(fb, g.N, i, o, m, n0)), ...);
-            ((st.g[a][P] = pull<S, T, P>(gb, g.N, i, o, m, n0)), ...);
-        }(std::make_integer_sequence<int, Q>{});
+        T fl[Q], gl[Q];
+        T *f = KEEP ? st.f[KEEP ? a : 0] : fl;
+        T *gq = KEEP ? st.g[KEEP ? a : 0] : gl;
+        pull_species<S, T, SOLID>(g, src, a, n0, i, o, m, f, gq);
         T n = 0, Pit = 0, Jt[3] = {0, 0, 0};
         [&]<int... P>(std::integer_sequence<int, P...>) {
-            ((n += st.f[a][P]), ...);
-            ((Pit += st.g[a][P]), ...);
-            ((Jt[0] += (T)cx(P) * st.g[a][P]), ...);
-            ((Jt[1] += (T)cy(P) * st.g[a][P]), ...);
-            ((Jt[2] += (T)cz(P) * st.g[a][P]), ...);
+            ((n += f[P]), ...);
+            ((Pit += gq[P]), ...);
+            ((Jt[0] += (T)cx(P) * gq[P]), ...);
+            ((Jt[1] += (T)cy(P) * gq[P]), ...);
+            ((Jt[2] += (T)cz(P) * gq[P]), ...);
         }(std::make_integer_sequence<int, Q>{});
         const T *Ca = C + (long long)a * 3 * g.N + i;
         const T *Fa = F + (long long)a * 3 * g.N + i;
@@ -415,8 +385,9 @@ __device__ __forceinline__ int plane_index(const Grid &g, int axis, int x, int y
     return axis == 0 ? y + g.ny * z : (axis == 1 ? x + g.nx * z : x + g.nx * y);
 }
 
-template <typename S, typename T, int M>
-__global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ src, S *__restrict__ dst,
+template <typename S, typename T, int M, bool SOLID>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (M == 1 ? 3 : 2) : 1)
+    k_collide(Grid g, const S *__restrict__ src, S *__restrict__ dst,
                                                 const uint32_t *__restrict__ mask, const T *__restrict__ C,
                                                 const T *__restrict__ F, StepParams sp,
                                                 double *__restrict__ flux_buf) {
@@ -424,7 +395,7 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
-    const uint32_t m = mask[i];
+    const uint32_t m = SOLID ? mask[i] : 0u;
     const int coord = sp.flux_axis == 0 ? x : (sp.flux_axis == 1 ? y : z);
     const bool on_plane = sp.flux_axis >= 0 && coord == sp.flux_plane;
     const int psize = sp.flux_axis == 0 ? g.ny * g.nz : (sp.flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
@@ -434,8 +405,9 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
         return;
     }
     const NbrOff o = nbr_offsets(g, x, y, z);
-    NodeState<S, T, M> st;
-    load_moments<S, T, M>(g, src, C, F, sp, i, o, m, st);
+    constexpr bool KEEP = (M == 1);
+    NodeState<S, T, M, KEEP> st;
+    load_moments<S, T, M, SOLID, KEEP>(g, src, C, F, sp, i, o, m, st);
     if (on_plane) {
 #pragma unroll
         for (int a = 0; a < M; ++a)
@@ -457,6 +429,17 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
         const T om = (T)sp.sp[a].omega_eff;
         const T inv = (T)sp.sp[a].inv;
         const T in0 = sp.sp[a].n0 > 0.0 ? (T)(1.0 / sp.sp[a].n0) : (T)0;
+        T fl[Q], gl[Q];
+        const T *fa = st.f[0];
+        const T *ga = st.g[0];
+        if constexpr (KEEP) {
+            fa = st.f[KEEP ? a : 0];
+            ga = st.g[KEEP ? a : 0];
+        } else {
+            pull_species<S, T, SOLID>(g, src, a, (T)sp.sp[a].n0, i, o, m, fl, gl);
+            fa = fl;
+            ga = gl;
+        }
         S *fo = dst + pop_off(a, 0, 0, g.N) + i;
         S *go = dst + pop_off(a, 1, 0, g.N) + i;
         [&]<int... P>(std::integer_sequence<int, P...>) {
@@ -473,8 +456,8 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
                     const T geq = w * (B + t1);
                     const T Sf = w * (sf0 + (T)3 * cX + (T)9 * cX * cua);
                     const T Sg = w * (sf0 + (T)3 * cY + (T)18 * cC * cua + (T)9 * cY * cua);
-                    const T fs = st.f[a][P] + om * (feq - st.f[a][P]) + inv * Sf;
-                    const T gs = st.g[a][P] + om * (geq - st.g[a][P]) + inv * Sg;
+                    const T fs = fa[P] + om * (feq - fa[P]) + inv * Sf;
+                    const T gs = ga[P] + om * (geq - ga[P]) + inv * Sg;
                     constexpr T iw = (T)(1.0 / wq(P));
                     Store<S, T>::store(fo + (long long)P * g.N, fs, iw * in0);
                     Store<S, T>::store(go + (long long)P * g.N, gs, iw * in0);
@@ -484,36 +467,32 @@ __global__ void __launch_bounds__(NT) k_collide(Grid g, const S *__restrict__ sr
     }
 }
 
-template <typename S, typename T>
+template <typename S, typename T, bool SOLID>
 static cudaError_t collide_m(int M, const Grid &g, const void *src, void *dst, const uint32_t *mask, const void *C,
                              const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
+#define LBE_COLLIDE(MM)                                                                                   \
+    k_collide<S, T, MM, SOLID><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, \
+                                                  sp, flux_buf)
     switch (M) {
-        case 1:
-            k_collide<S, T, 1><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
-                                                  flux_buf);
-            break;
-        case 2:
-            k_collide<S, T, 2><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
-                                                  flux_buf);
-            break;
-        case 3:
-            k_collide<S, T, 3><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
-                                                  flux_buf);
-            break;
-        case 4:
-            k_collide<S, T, 4><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, sp,
-                                                  flux_buf);
-            break;
+        case 1: LBE_COLLIDE(1); break;
+        case 2: LBE_COLLIDE(2); break;
+        case 3: LBE_COLLIDE(3); break;
+        case 4: LBE_COLLIDE(4); break;
         default: return cudaErrorInvalidValue;
     }
+#undef LBE_COLLIDE
     return cudaGetLastError();
 }
 
-cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, const void *C,
-                           const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
+cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
+                           const void *C, const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
-    LBE_DISPATCH_PREC(p, (e = collide_m<S, T>(sp.M, g, src, dst, mask, C, F, sp, flux_buf, st)));
+    if (solid) {
+        LBE_DISPATCH_PREC(p, (e = collide_m<S, T, true>(sp.M, g, src, dst, mask, C, F, sp, flux_buf, st)));
+    } else {
+        LBE_DISPATCH_PREC(p, (e = collide_m<S, T, false>(sp.M, g, src, dst, mask, C, F, sp, flux_buf, st)));
+    }
     return e;
 }
 
@@ -535,8 +514,8 @@ __global__ void __launch_bounds__(NT) k_moments(Grid g, const S *__restrict__ sr
         return;
     }
     const NbrOff o = nbr_offsets(g, x, y, z);
-    NodeState<S, T, M> st;
-    load_moments<S, T, M>(g, src, C, F, sp, i, o, m, st);
+    NodeState<S, T, M, false> st;
+    load_moments<S, T, M, true, false>(g, src, C, F, sp, i, o, m, st);
     for (int a = 0; a < M; ++a) {
         nout[(long long)a * g.N + i] = (double)st.n[a];
         for (int c = 0; c < 3; ++c) Jout[((long long)a * 3 + c) * g.N + i] = (double)st.J[a][c];

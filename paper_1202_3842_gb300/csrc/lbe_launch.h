@@ -37,8 +37,25 @@ struct ContactParams {
     double s_ab[MAXS][MAXS];   // sigma_a sigma_b / (sigma_a + sigma_b)
     double xi2c[MAXS];         // (pi/6) sigma_b^2
     double xi3c[MAXS];         // (pi/6) sigma_b^3
-    int ball_start[MAXS];      // first entry of species b in the ball offset table
-    int ball_count[MAXS];
+};
+
+// Rows of the averaging ball |d| <= sigma_b/2 of every species: row k of
+// species b covers d = (-a..a, dy, dz).
+struct BallRows {
+    int nrows[MAXS];
+    int count[MAXS];
+    signed char dy[MAXS][81], dz[MAXS][81], a[MAXS][81];
+};
+
+struct ContactLaunch {
+    const Grid *grid;
+    const CUtensorMap *maps;  // one per species (padded density, box from contact_box)
+    const ContactParams *cp;
+    const BallRows *br;
+    int RB;                   // largest ball half-width
+    void *gab;
+    void *gnpad;
+    int *err;
 };
 
 struct ShellLaunch {
@@ -66,19 +83,19 @@ cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const
 cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
                               double n0, cudaStream_t st);
 // K1: density (pulled zeroth moment) of every species into the padded field.
-cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, int M,
+// solid = false: no solid node and every axis periodic (the link mask is not read).
+cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
                            const double *n0, void *npad, int *err, cudaStream_t st);
 // K2: ball averages, BMCSL contact values g_ab [M][M][N] and padded g_ab*n_b [M][M][P].
-// ball: padded linear offsets of every species' averaging ball (see ContactParams).
-cudaError_t launch_contact(bool fp64, const Grid &g, const ContactParams &cp, const int *ball, const void *npad,
-                           void *gab, void *gnpad, int *err, cudaStream_t st);
+cudaError_t launch_contact_tma(bool fp64, const ContactLaunch &L, cudaStream_t st);
+void contact_box(bool fp64, int M, int RB, int *bx, int *by);
 // K3: shell force of one ordered pair.
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st);
 bool shell_supported(bool fp64, int S);
 void shell_box(bool fp64, int S, int *bx, int *by);
 int half_shell_host(int S, int *e, int cap);
 // K4: fused moments + DD-TR collision + pull streaming.
-cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask,
+cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf,
                            cudaStream_t st);
 // Moments of the current state (FP64 out): n [M][N], J [M][3][N].
