@@ -303,25 +303,27 @@ lbe_status prepare(lbe_ctx *c) {
         g.py = g.ny + 2 * H;
         g.pz = g.nz + 2 * H;
         g.P = (long long)g.px * g.py * g.pz;
-        // averaging ball |d| <= sigma_b/2 as rows (dy, dz) of half-width a along x
+        // averaging ball |d| <= sigma_b/2 as rows (dy, dz) of half-width a along x, grouped by dz
         BallRows br{};
         for (int b = 0; b < c->M; ++b) {
             const double R = 0.5 * c->sigma[b], R2 = R * R;
             const int Ri = (int)std::floor(R);
             int nr = 0, cnt = 0;
-            for (int dz = -Ri; dz <= Ri; ++dz)
+            for (int dz = -4; dz <= 4; ++dz) {
+                br.first[b][dz + 4] = (short)nr;
+                if (dz < -Ri || dz > Ri) continue;
                 for (int dy = -Ri; dy <= Ri; ++dy) {
                     const double rem = R2 - (double)(dy * dy + dz * dz);
                     if (rem < 0.0) continue;
                     int a = 0;
                     while ((double)((a + 1) * (a + 1)) <= rem) ++a;
                     br.dy[b][nr] = (signed char)dy;
-                    br.dz[b][nr] = (signed char)dz;
                     br.a[b][nr] = (signed char)a;
                     cnt += 2 * a + 1;
                     ++nr;
                 }
-            br.nrows[b] = nr;
+            }
+            br.first[b][9] = (short)nr;
             br.count[b] = cnt;
         }
         c->brows = br;

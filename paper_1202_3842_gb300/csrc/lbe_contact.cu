@@ -91,19 +91,28 @@ __global__ void __launch_bounds__(256)
         if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) return;
         if (active) {
             T xi2 = 0, xi3 = 0, nloc[M];
+            const T *sb[2 * RB + 1];
+#pragma unroll
+            for (int k = 0; k <= 2 * RB; ++k) sb[k] = ring + ((iz + k) % Tl::R) * SLOT + toff;
 #pragma unroll
             for (int b = 0; b < M; ++b) {
                 T acc = 0;
-                const int nr = br.nrows[b];
-                for (int k = 0; k < nr; ++k) {
-                    const int dy = br.dy[b][k], dz = br.dz[b][k], a = br.a[b][k];
-                    const T *row = ring + ((iz + RB + dz) % Tl::R) * SLOT + b * PL + toff + dy * Tl::BX;
-                    for (int dx = -a; dx <= a; ++dx) acc += row[dx];
+#pragma unroll
+                for (int dz = -RB; dz <= RB; ++dz) {
+                    const T *pz = sb[dz + RB] + b * PL;
+                    const int k0 = br.first[b][dz + 4], k1 = br.first[b][dz + 5];
+                    for (int k = k0; k < k1; ++k) {
+                        const int a = br.a[b][k];
+                        const T *row = pz + br.dy[b][k] * Tl::BX;
+#pragma unroll
+                        for (int dx = -RB; dx <= RB; ++dx)
+                            if (dx >= -a && dx <= a) acc += row[dx];
+                    }
                 }
                 const T nbar = acc / (T)br.count[b];
                 xi2 += (T)cp.xi2c[b] * nbar;
                 xi3 += (T)cp.xi3c[b] * nbar;
-                nloc[b] = ring[((iz + RB) % Tl::R) * SLOT + b * PL + toff];
+                nloc[b] = sb[RB][b * PL];
             }
             const T i1 = (T)1 / ((T)1 - xi3);
             if (!(xi3 < (T)1)) atomicOr(err, ERR_PACKING);

@@ -40,11 +40,12 @@ struct ContactParams {
 };
 
 // Rows of the averaging ball |d| <= sigma_b/2 of every species: row k of
-// species b covers d = (-a..a, dy, dz).
+// species b covers d = (-a..a, dy, dz); rows are grouped by dz, the rows with
+// dz = z being first[b][z + 4] .. first[b][z + 5] - 1.
 struct BallRows {
-    int nrows[MAXS];
     int count[MAXS];
-    signed char dy[MAXS][81], dz[MAXS][81], a[MAXS][81];
+    short first[MAXS][10];
+    signed char dy[MAXS][81], a[MAXS][81];
 };
 
 struct ContactLaunch {
@@ -93,7 +94,6 @@ void contact_box(bool fp64, int M, int RB, int *bx, int *by);
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st);
 bool shell_supported(bool fp64, int S);
 void shell_box(bool fp64, int S, int *bx, int *by);
-int half_shell_host(int S, int *e, int cap);
 // K4: fused moments + DD-TR collision + pull streaming.
 cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf,

@@ -76,4 +76,63 @@ struct ShellTile {
     static constexpr int LZ = 32;
 };
 
+// Column organisation of the half shell for the z-blocked kernel: column
+// pairs (ex, ey) / (-ex, -ey) with ex > 0 or (ex == 0, ey > 0); mask bit
+// (ez + S) is set when (ex, ey, ez) lies in the shell.  The centre column
+// (0, 0) holds ez = +-S only and is handled on its own.
+__host__ __device__ constexpr int column_count(int S) {
+    int c = 0;
+    for (int y = -S; y <= S; ++y)
+        for (int x = 0; x <= S; ++x) {
+            if (!(x > 0 || y > 0)) continue;
+            bool any = false;
+            for (int z = -S; z <= S; ++z) any = any || in_shell(S, x, y, z);
+            if (any) ++c;
+        }
+    return c;
+}
+
+template <int K>
+struct Columns {
+    int ex[K], ey[K];
+    unsigned mask[K];
+};
+
+template <int S>
+__host__ __device__ constexpr Columns<column_count(S)> make_columns() {
+    Columns<column_count(S)> t{};
+    int c = 0;
+    for (int y = -S; y <= S; ++y)
+        for (int x = 0; x <= S; ++x) {
+            if (!(x > 0 || y > 0)) continue;
+            unsigned m = 0;
+            for (int z = -S; z <= S; ++z)
+                if (in_shell(S, x, y, z)) m |= 1u << (z + S);
+            if (m) {
+                t.ex[c] = x;
+                t.ey[c] = y;
+                t.mask[c] = m;
+                ++c;
+            }
+        }
+    return t;
+}
+
+// Tile of the z-blocked shell kernel: 32 x 8 threads, TZ outputs per thread
+// along z; the ring holds the 2S + TZ planes in use plus TZ in flight.
+template <typename T, int S, int TZ>
+struct ShellTileZ {
+    static constexpr int A = 16 / (int)sizeof(T);
+    static constexpr int TX = 32;
+    static constexpr int TY = 8;
+    static constexpr int BX = ((TX + 2 * S + A - 1) + A - 1) / A * A;
+    static constexpr int BY = TY + 2 * S;
+    static constexpr int R = 2 * S + 2 * TZ;
+    static constexpr int PLANE = BX * BY;
+    static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
+    static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;
+    static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
+    static constexpr int LZ = 32;  // multiple of TZ
+};
+
 }  // namespace lbe

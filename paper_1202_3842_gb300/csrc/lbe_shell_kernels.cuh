@@ -1,0 +1,380 @@
+// Kernel templates of the mean-field shell force (K3) and their launchers.
+// Included by the translation units that instantiate them (one group of pair
+// diameters each, so the builds run in parallel).
+//
+// K3: mean-field Enskog force of one ordered species pair (a, b) (Appendix,
+// hard-sphere C^{alpha,mf}):
+//   C^a(r) (+)= -kT sigma_ab^2 w_ab n_a(r) sum_{e in K_ab} e^ (g_ab(r) + g_ab(r+e))/2 n_b(r+e)
+//            =  coef * n_a(r) * [ g_ab(r)/2 * sum e^ n_b(r+e) + 1/2 * sum e^ (g_ab n_b)(r+e) ]
+// with coef = -kT sigma_ab^2 w_ab.  Both sums run over the half shell as
+// e^ [a(r+e) - a(r-e)].
+//
+// Data path: the padded density n_b and the padded product g_ab*n_b are
+// streamed plane by plane (z-marching) into a shared-memory ring by TMA
+// (cp.async.bulk.tensor, one 2-D box of (32 + 2S) x (TY + 2S) per field and
+// plane, completion on an mbarrier per ring slot).  The plain kernel gives
+// each thread one output per plane; the z-blocked kernel gives each thread TZ
+// outputs along z and reuses every shared-memory read across them.  The shell
+// offsets and unit vectors are compile-time immediates.
+#pragma once
+#include <utility>
+
+#include "lbe_device.cuh"
+#include "lbe_launch.h"
+#include "lbe_shell.cuh"
+
+namespace lbe {
+
+template <int S>
+struct ShellTable {
+    static constexpr auto hs = make_half_shell<S>();
+    static constexpr int count = half_shell_count(S);
+};
+
+template <typename T, int S, int I>
+__device__ __forceinline__ void shell_term(const T *const *sb, T *an, T *ag) {
+    using Tl = ShellTile<T, S>;
+    constexpr int ex = ShellTable<S>::hs.e[I][0];
+    constexpr int ey = ShellTable<S>::hs.e[I][1];
+    constexpr int ez = ShellTable<S>::hs.e[I][2];
+    constexpr double len = ct_sqrt((double)(ex * ex + ey * ey + ez * ez));
+    constexpr int off = ey * Tl::BX + ex;
+    constexpr int GN = Tl::PLANE_BYTES / (int)sizeof(T);
+    const T *pp = sb[S + ez] + off;
+    const T *pm = sb[S - ez] - off;
+    const T dn = pp[0] - pm[0];
+    const T dg = pp[GN] - pm[GN];
+    if constexpr (ex != 0) {
+        constexpr T u = (T)(ex / len);
+        an[0] += u * dn;
+        ag[0] += u * dg;
+    }
+    if constexpr (ey != 0) {
+        constexpr T u = (T)(ey / len);
+        an[1] += u * dn;
+        ag[1] += u * dg;
+    }
+    if constexpr (ez != 0) {
+        constexpr T u = (T)(ez / len);
+        an[2] += u * dn;
+        ag[2] += u * dg;
+    }
+}
+
+template <typename T, int S, int... I>
+__device__ __forceinline__ void shell_sum(const T *const *sb, T *an, T *ag, std::integer_sequence<int, I...>) {
+    (shell_term<T, S, I>(sb, an, ag), ...);
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(32 * ShellTile<T, S>::TY)
+    k_shell_force(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn,
+                  Grid g, int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab,
+                  T *__restrict__ Cout, T coef, int accumulate, int *err) {
+    using Tl = ShellTile<T, S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    T *ring = reinterpret_cast<T *>(base);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
+    constexpr int SLOT = Tl::SLOT_BYTES / (int)sizeof(T);
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::LZ;
+    const int zend = min(z0 + Tl::LZ, g.nz);
+    const int nout = zend - z0;
+    const int nplanes = nout + 2 * S;
+    const bool leader = (tx == 0 && ty == 0);
+    const int bx = x0 + g.H - S - ox;  // multiple of 16 bytes / sizeof(T)
+    const int by = y0 + g.H - S;
+    constexpr uint32_t tx_bytes = 2u * Tl::PLANE * (uint32_t)sizeof(T);
+
+    if (leader) {
+        prefetch_tensormap(&map_n);
+        prefetch_tensormap(&map_gn);
+        for (int r = 0; r < Tl::R; ++r) mbar_init(&bars[r], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int j) {  // plane j holds interior z = z0 - S + j
+        const int slot = j % Tl::R;
+        unsigned char *dst = base + slot * Tl::SLOT_BYTES;
+        const int zp = z0 - S + j + g.H;
+        mbar_arrive_expect_tx(&bars[slot], tx_bytes);
+        tma_load_3d(dst, &map_n, bx, by, zp, &bars[slot]);
+        tma_load_3d(dst + Tl::PLANE_BYTES, &map_gn, bx, by, zp, &bars[slot]);
+    };
+    if (leader) {
+        for (int j = 0; j < 2 * S + 1 && j < nplanes; ++j) issue(j);
+    }
+    for (int j = 0; j < 2 * S; ++j)
+        if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < g.nx) && (y < g.ny);
+    const int toff = (ty + S) * Tl::BX + (tx + S + ox);
+    const T half = (T)0.5;
+
+    for (int iz = 0; iz < nout; ++iz) {
+        if (leader && iz + 2 * S + 1 < nplanes) {
+            fence_proxy_async_smem();
+            issue(iz + 2 * S + 1);
+        }
+        const int jn = iz + 2 * S;
+        if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) return;
+        if (active) {
+            const T *sb[2 * S + 1];
+#pragma unroll
+            for (int k = 0; k <= 2 * S; ++k) sb[k] = ring + ((iz + k) % Tl::R) * SLOT + toff;
+            T an[3] = {0, 0, 0}, ag[3] = {0, 0, 0};
+            shell_sum<T, S>(sb, an, ag, std::make_integer_sequence<int, ShellTable<S>::count>{});
+            const int z = z0 + iz;
+            const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+            const T na = npad_a[pidx(g, x, y, z)];
+            const T gr = g_ab[i];
+            const T pre = coef * na;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const T v = pre * (half * gr * an[c] + half * ag[c]);
+                T *o = Cout + (long long)c * g.N + i;
+                if (accumulate)
+                    *o += v;
+                else
+                    *o = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// z-blocked variant (FP32): each thread produces TZ outputs along z.  The half
+// shell is walked as column pairs (ex, ey) / (-ex, -ey); every input value of
+// a column within the planes t + D (t < TZ, D the column's z-offsets) is read
+// from shared memory once and reused by all TZ outputs:
+//   d_t(ez) = a(x+ex, y+ey, z+t+ez) - a(x-ex, y-ey, z+t-ez),  ez in D,
+//   acc_t  += (ex, ey, ez)/|e| * d_t(ez).
+// The centre column (0, 0, +-S) contributes only to the z component.
+// ---------------------------------------------------------------------------
+template <int S>
+struct ColTable {
+    static constexpr auto cols = make_columns<S>();
+    static constexpr int count = column_count(S);
+};
+
+template <int S, int TZ>
+__host__ __device__ constexpr bool col_needs(unsigned mask, int k) {
+    // plane offset k (relative to the first output) is read by some output t
+    for (int t = 0; t < TZ; ++t) {
+        int ez = k - t;
+        if (ez >= -S && ez <= S && (mask >> (ez + S)) & 1u) return true;
+    }
+    return false;
+}
+
+template <typename T, int S, int TZ, int I>
+__device__ __forceinline__ void column_pair(const T *const *sb, T (*an)[3], T (*ag)[3]) {
+    using Tl = ShellTileZ<T, S, TZ>;
+    constexpr int ex = ColTable<S>::cols.ex[I];
+    constexpr int ey = ColTable<S>::cols.ey[I];
+    constexpr unsigned mask = ColTable<S>::cols.mask[I];
+    constexpr int offc = ey * Tl::BX + ex;
+    constexpr int GN = Tl::PLANE_BYTES / (int)sizeof(T);
+    constexpr int NK = 2 * S + TZ;  // plane offsets k = -S .. S + TZ - 1
+    T cn[NK], cg[NK], mn[NK], mg[NK];
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+        (
+            [&] {
+                constexpr int k = K - S;
+                if constexpr (col_needs<S, TZ>(mask, k)) {
+                    const T *p = sb[K];
+                    cn[K] = p[offc];
+                    cg[K] = p[offc + GN];
+                    mn[K] = p[-offc];
+                    mg[K] = p[-offc + GN];
+                }
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, NK>{});
+    [&]<int... J>(std::integer_sequence<int, J...>) {
+        (
+            [&] {
+                constexpr int t = J / (2 * S + 1);
+                constexpr int ez = J % (2 * S + 1) - S;
+                if constexpr ((mask >> (ez + S)) & 1u) {
+                    constexpr double len = ct_sqrt((double)(ex * ex + ey * ey + ez * ez));
+                    const T dn = cn[t + ez + S] - mn[t - ez + S];
+                    const T dg = cg[t + ez + S] - mg[t - ez + S];
+                    if constexpr (ex != 0) {
+                        constexpr T u = (T)(ex / len);
+                        an[t][0] += u * dn;
+                        ag[t][0] += u * dg;
+                    }
+                    if constexpr (ey != 0) {
+                        constexpr T u = (T)(ey / len);
+                        an[t][1] += u * dn;
+                        ag[t][1] += u * dg;
+                    }
+                    if constexpr (ez != 0) {
+                        constexpr T u = (T)(ez / len);
+                        an[t][2] += u * dn;
+                        ag[t][2] += u * dg;
+                    }
+                }
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, TZ *(2 * S + 1)>{});
+}
+
+template <typename T, int S, int TZ, int... I>
+__device__ __forceinline__ void all_columns(const T *const *sb, T (*an)[3], T (*ag)[3],
+                                            std::integer_sequence<int, I...>) {
+    (column_pair<T, S, TZ, I>(sb, an, ag), ...);
+}
+
+template <typename T, int S, int TZ>
+__global__ void __launch_bounds__(256, 1)
+    k_shell_force_zb(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn, Grid g,
+                     int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab, T *__restrict__ Cout, T coef,
+                     int accumulate, int *err) {
+    using Tl = ShellTileZ<T, S, TZ>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    T *ring = reinterpret_cast<T *>(base);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
+    constexpr int SLOT = Tl::SLOT_BYTES / (int)sizeof(T);
+    constexpr int GN = Tl::PLANE_BYTES / (int)sizeof(T);
+    constexpr int NK = 2 * S + TZ;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::LZ;
+    const int zend = min(z0 + Tl::LZ, g.nz);
+    const int nsuper = (zend - z0 + TZ - 1) / TZ;
+    const int nplanes = nsuper * TZ + 2 * S;
+    const bool leader = (tx == 0 && ty == 0);
+    const int bx = x0 + g.H - S - ox;
+    const int by = y0 + g.H - S;
+    constexpr uint32_t tx_bytes = 2u * Tl::PLANE * (uint32_t)sizeof(T);
+
+    if (leader) {
+        prefetch_tensormap(&map_n);
+        prefetch_tensormap(&map_gn);
+        for (int r = 0; r < Tl::R; ++r) mbar_init(&bars[r], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int j) {  // plane j holds interior z = z0 - S + j
+        const int slot = j % Tl::R;
+        unsigned char *dst = base + slot * Tl::SLOT_BYTES;
+        const int zp = z0 - S + j + g.H;
+        mbar_arrive_expect_tx(&bars[slot], tx_bytes);
+        tma_load_3d(dst, &map_n, bx, by, zp, &bars[slot]);
+        tma_load_3d(dst + Tl::PLANE_BYTES, &map_gn, bx, by, zp, &bars[slot]);
+    };
+    if (leader)
+        for (int j = 0; j < Tl::R && j < nplanes; ++j) issue(j);
+
+    const int x = x0 + tx, y = y0 + ty;
+    const bool active = (x < g.nx) && (y < g.ny);
+    const int toff = (ty + S) * Tl::BX + (tx + S + ox);
+    const T half = (T)0.5;
+
+    for (int s = 0; s < nsuper; ++s) {
+        const int j0 = s * TZ;
+        for (int j = j0; j < j0 + NK; ++j)
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+        if (active) {
+            const T *sb[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) sb[k] = ring + ((j0 + k) % Tl::R) * SLOT + toff;
+            T an[TZ][3], ag[TZ][3];
+#pragma unroll
+            for (int t = 0; t < TZ; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    an[t][c] = (T)0;
+                    ag[t][c] = (T)0;
+                }
+            // centre column (0, 0, +-S): e^ = (0, 0, 1) for ez = +S
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                an[t][2] += sb[t + 2 * S][0] - sb[t][0];
+                ag[t][2] += sb[t + 2 * S][GN] - sb[t][GN];
+            }
+            all_columns<T, S, TZ>(sb, an, ag, std::make_integer_sequence<int, ColTable<S>::count>{});
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                const int z = z0 + j0 + t;
+                if (z < zend) {
+                    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+                    const T na = npad_a[pidx(g, x, y, z)];
+                    const T gr = g_ab[i];
+                    const T pre = coef * na;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const T v = pre * (half * gr * an[t][c] + half * ag[t][c]);
+                        T *o = Cout + (long long)c * g.N + i;
+                        if (accumulate)
+                            *o += v;
+                        else
+                            *o = v;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (leader) {
+            fence_proxy_async_smem();
+            for (int j = j0 + Tl::R; j < j0 + Tl::R + TZ && j < nplanes; ++j) issue(j);
+        }
+    }
+}
+
+template <typename T, int S, int TZ>
+cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
+    using Tl = ShellTileZ<T, S, TZ>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_shell_force_zb<T, S, TZ>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, Tl::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const Grid &g = *L.grid;
+    dim3 block(Tl::TX, Tl::TY, 1);
+    dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
+    const int ox = ((g.H - S) % Tl::A + Tl::A) % Tl::A;
+    k_shell_force_zb<T, S, TZ><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
+                                                              (const T *)L.g_ab, (T *)L.Cout, (T)L.coef,
+                                                              L.accumulate, L.err);
+    return cudaGetLastError();
+}
+
+template <typename T, int S>
+cudaError_t launch_one(const ShellLaunch &L, cudaStream_t st) {
+    using Tl = ShellTile<T, S>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_shell_force<T, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Tl::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const Grid &g = *L.grid;
+    dim3 block(Tl::TX, Tl::TY, 1);
+    dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
+    const int A = Tl::A;
+    const int ox = ((g.H - S) % A + A) % A;
+    k_shell_force<T, S><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
+                                                       (const T *)L.g_ab, (T *)L.Cout, (T)L.coef, L.accumulate,
+                                                       L.err);
+    return cudaGetLastError();
+}
+
+}  // namespace lbe

@@ -136,7 +136,8 @@ def test_fp64_parity_channel_mixture_with_flux():
 
 
 def test_fp64_parity_ideal_gas_and_consistent_moments():
-    w, arr = case_well((20, 18, 16), 0.0, 0.0, 0.9, 1.0, 3.0)
+    w, arr = case_well((20, 18, 16), 3.0, 0.1, 0.9, 1.0, 3.0)
+    w["sigma"] = [0.0]  # ideal gas: no mean-field force
     arr["n"] = arr["n"] * 0 + 0.01
     g = setup_gpu(w, arr, "fp64")
     o = setup_oracle(w, arr)
