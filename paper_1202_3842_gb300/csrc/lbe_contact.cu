@@ -29,7 +29,7 @@ struct ContactTile {
     static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = M * PLANE_BYTES;
     static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
-    static constexpr int LZ = 32;
+    static constexpr int LZ = 8;
 };
 
 struct ContactMaps {

@@ -1,5 +1,7 @@
 // Dispatch of the shell-force kernels by precision and pair diameter, and the
-// host-side shell helpers.  The kernels are instantiated in lbe_shell_f32_*.cu
+// host-side shell helpers.  FP32 pair diameters up to 7 use the z-blocked
+// kernel (two outputs per thread along z, 32 x 16 threads); diameter 8 and the
+// FP64 path use the plain kernel (one output per thread and plane).  The kernels are instantiated in lbe_shell_f32_*.cu
 // and lbe_shell_f64.cu.
 #include "lbe_device.cuh"
 #include "lbe_launch.h"
@@ -9,20 +11,22 @@ namespace lbe {
 
 template <typename T, int S>
 cudaError_t launch_one(const ShellLaunch &L, cudaStream_t st);
-template <typename T, int S, int TZ>
+template <typename T, int S, int TZ, int TYB>
 cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st);
+
+
 
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st) {
     if (!fp64) {
         switch (S) {
-            case 1: return launch_zb<float, 1, 4>(L, st);
-            case 2: return launch_zb<float, 2, 4>(L, st);
-            case 3: return launch_zb<float, 3, 4>(L, st);
-            case 4: return launch_zb<float, 4, 4>(L, st);
-            case 5: return launch_zb<float, 5, 4>(L, st);
-            case 6: return launch_zb<float, 6, 4>(L, st);
-            case 7: return launch_zb<float, 7, 4>(L, st);
-            case 8: return launch_zb<float, 8, 2>(L, st);
+            case 1: return launch_zb<float, 1, 2, 16>(L, st);
+            case 2: return launch_zb<float, 2, 2, 16>(L, st);
+            case 3: return launch_zb<float, 3, 2, 16>(L, st);
+            case 4: return launch_zb<float, 4, 2, 16>(L, st);
+            case 5: return launch_zb<float, 5, 2, 16>(L, st);
+            case 6: return launch_zb<float, 6, 2, 16>(L, st);
+            case 7: return launch_zb<float, 7, 2, 16>(L, st);
+            case 8: return launch_one<float, 8>(L, st);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -42,8 +46,9 @@ bool shell_supported(bool fp64, int S) { return S >= 1 && S <= (fp64 ? 7 : 8); }
 
 void shell_box(bool fp64, int S, int *bx, int *by) {
     if (!fp64) {
-        *bx = ((32 + 2 * S + 3) + 3) / 4 * 4;  // ShellTileZ<float, S, TZ>::BX
-        *by = 8 + 2 * S;
+        const int zb = S <= 7;  // z-blocked tiles are 32 x 16 outputs per plane, the plain ones 32 x 8
+        *bx = ((32 + 2 * S + 3) + 3) / 4 * 4;  // same for ShellTile and ShellTileZ
+        *by = (zb ? 16 : 8) + 2 * S;
         return;
     }
 #define LBE_BOX(s)                              \

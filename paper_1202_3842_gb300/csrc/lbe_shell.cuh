@@ -73,7 +73,7 @@ struct ShellTile {
     static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;  // density plane + g*n plane
     static constexpr int SMEM = R * SLOT_BYTES + 256 /*barriers*/ + 128 /*alignment*/;
-    static constexpr int LZ = 32;
+    static constexpr int LZ = 16;
 };
 
 // Column organisation of the half shell for the z-blocked kernel: column
@@ -118,13 +118,13 @@ __host__ __device__ constexpr Columns<column_count(S)> make_columns() {
     return t;
 }
 
-// Tile of the z-blocked shell kernel: 32 x 8 threads, TZ outputs per thread
+// Tile of the z-blocked shell kernel: 32 x TYB threads, TZ outputs per thread
 // along z; the ring holds the 2S + TZ planes in use plus TZ in flight.
-template <typename T, int S, int TZ>
+template <typename T, int S, int TZ, int TYB = 16>
 struct ShellTileZ {
     static constexpr int A = 16 / (int)sizeof(T);
     static constexpr int TX = 32;
-    static constexpr int TY = 8;
+    static constexpr int TY = TYB;
     static constexpr int BX = ((TX + 2 * S + A - 1) + A - 1) / A * A;
     static constexpr int BY = TY + 2 * S;
     static constexpr int R = 2 * S + 2 * TZ;
@@ -132,7 +132,7 @@ struct ShellTileZ {
     static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;
     static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
-    static constexpr int LZ = 32;  // multiple of TZ
+    static constexpr int LZ = 16;  // multiple of TZ
 };
 
 }  // namespace lbe

@@ -1,6 +1,7 @@
-// Instantiation of the z-blocked FP32 shell-force kernel for pair diameters 5.
+// Explicit instantiations of the FP32 shell-force kernels.
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_zb<float, 5, 4>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<float, 5, 2, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<float, 6, 2, 16>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

@@ -1,6 +1,6 @@
-// Instantiation of the z-blocked FP32 shell-force kernel for pair diameters 6.
+// Explicit instantiations of the FP32 shell-force kernels.
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_zb<float, 6, 4>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<float, 7, 2, 16>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

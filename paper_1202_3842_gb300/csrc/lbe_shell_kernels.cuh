@@ -177,9 +177,9 @@ __host__ __device__ constexpr bool col_needs(unsigned mask, int k) {
     return false;
 }
 
-template <typename T, int S, int TZ, int I>
+template <typename T, int S, int TZ, int TYB, int I>
 __device__ __forceinline__ void column_pair(const T *const *sb, T (*an)[3], T (*ag)[3]) {
-    using Tl = ShellTileZ<T, S, TZ>;
+    using Tl = ShellTileZ<T, S, TZ, TYB>;
     constexpr int ex = ColTable<S>::cols.ex[I];
     constexpr int ey = ColTable<S>::cols.ey[I];
     constexpr unsigned mask = ColTable<S>::cols.mask[I];
@@ -231,18 +231,18 @@ __device__ __forceinline__ void column_pair(const T *const *sb, T (*an)[3], T (*
     }(std::make_integer_sequence<int, TZ *(2 * S + 1)>{});
 }
 
-template <typename T, int S, int TZ, int... I>
+template <typename T, int S, int TZ, int TYB, int... I>
 __device__ __forceinline__ void all_columns(const T *const *sb, T (*an)[3], T (*ag)[3],
                                             std::integer_sequence<int, I...>) {
-    (column_pair<T, S, TZ, I>(sb, an, ag), ...);
+    (column_pair<T, S, TZ, TYB, I>(sb, an, ag), ...);
 }
 
-template <typename T, int S, int TZ>
-__global__ void __launch_bounds__(256, 1)
+template <typename T, int S, int TZ, int TYB>
+__global__ void __launch_bounds__(32 * TYB, 1)
     k_shell_force_zb(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn, Grid g,
                      int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab, T *__restrict__ Cout, T coef,
                      int accumulate, int *err) {
-    using Tl = ShellTileZ<T, S, TZ>;
+    using Tl = ShellTileZ<T, S, TZ, TYB>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(256, 1)
                 an[t][2] += sb[t + 2 * S][0] - sb[t][0];
                 ag[t][2] += sb[t + 2 * S][GN] - sb[t][GN];
             }
-            all_columns<T, S, TZ>(sb, an, ag, std::make_integer_sequence<int, ColTable<S>::count>{});
+            all_columns<T, S, TZ, TYB>(sb, an, ag, std::make_integer_sequence<int, ColTable<S>::count>{});
 #pragma unroll
             for (int t = 0; t < TZ; ++t) {
                 const int z = z0 + j0 + t;
@@ -336,12 +336,12 @@ __global__ void __launch_bounds__(256, 1)
     }
 }
 
-template <typename T, int S, int TZ>
+template <typename T, int S, int TZ, int TYB>
 cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
-    using Tl = ShellTileZ<T, S, TZ>;
+    using Tl = ShellTileZ<T, S, TZ, TYB>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_shell_force_zb<T, S, TZ>,
+        cudaError_t e = cudaFuncSetAttribute(k_shell_force_zb<T, S, TZ, TYB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Tl::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -350,7 +350,7 @@ cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
     dim3 block(Tl::TX, Tl::TY, 1);
     dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
     const int ox = ((g.H - S) % Tl::A + Tl::A) % Tl::A;
-    k_shell_force_zb<T, S, TZ><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
+    k_shell_force_zb<T, S, TZ, TYB><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
                                                               (const T *)L.g_ab, (T *)L.Cout, (T)L.coef,
                                                               L.accumulate, L.err);
     return cudaGetLastError();
