@@ -37,7 +37,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")  # JSON text
 FALLBACK_HBM_GBS = 6800.0
 SMS = 152
 FP32_LANES_PER_SM = 128
@@ -177,9 +177,9 @@ def source_hash(files):
 KERNEL_SOURCES = {
     "collide": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "shell": ["paper_1202_3842_gb300/csrc/lbe_shell.cu", "paper_1202_3842_gb300/csrc/lbe_shell.cuh",
-              "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+              "paper_1202_3842_gb300/csrc/lbe_shell_kernels.cuh", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
-    "contact": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "contact": ["paper_1202_3842_gb300/csrc/lbe_contact.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "flux": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu"],
 }
 
