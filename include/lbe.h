@@ -209,6 +209,22 @@ lbe_status lbe_get_stage_times(lbe_ctx *ctx, double *ms, long long *launches);
 /* Number of kernel launches this context has issued (all entry points). */
 lbe_status lbe_get_launch_count(lbe_ctx *ctx, long long *launches);
 
+/* Species masses mass[M] = sum over the lattice of n^s of the current state,
+ * like the mass of lbe_get_totals, but without allocating any device memory.
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate at the time of the call (the device memory pool is fully reserved
+ * by another framework, a loop cannot take the latency or synchronisation of
+ * an allocation, or the process keeps a fixed device-memory footprint).
+ * The block partial sums live in one file-scope device array of the library
+ * (4 x 4096 + 4 doubles, about 128 KiB, held by every GPU that loads the
+ * library until the process exits), so the lattice may have at most
+ * 4096 x 4096 = 16777216 nodes; larger lattices return LBE_ERR_UNSUPPORTED.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any CUDA stream capture.  All calls share the array (each
+ * call overwrites the parts it reads, the last call's contents stay behind);
+ * calls that overlap on the GPU race on it.  Synchronises the context stream. */
+lbe_status lbe_get_mass_noalloc(lbe_ctx *ctx, double *mass);
+
 const char *lbe_status_string(lbe_status status);
 const char *lbe_last_error(lbe_ctx *ctx);
 

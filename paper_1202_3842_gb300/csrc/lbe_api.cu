@@ -17,6 +17,15 @@
 
 using namespace lbe;
 
+namespace lbe {
+cudaError_t noalloc_scratch(int device, double **out);
+cudaError_t launch_mass_noalloc(int prec, int nx, int ny, int nz, const void *pop, const uint32_t *mask, int M,
+                                const double *n0, double *scratch, int nblocks, cudaStream_t st);
+long long noalloc_max_nodes();
+int noalloc_blocks(long long N);
+size_t noalloc_result_offset();
+}  // namespace lbe
+
 namespace {
 
 thread_local std::string t_last_error;
@@ -963,6 +972,27 @@ lbe_status lbe_get_stage_times(lbe_ctx *c, double *ms, long long *launches) {
         if (ms) ms[s] = c->stage_ms[s];
         if (launches) launches[s] = c->stage_launches[s];
     }
+    return LBE_OK;
+}
+
+lbe_status lbe_get_mass_noalloc(lbe_ctx *c, double *mass) {
+    TRY(ready(c));
+    if (!mass) return fail(c, LBE_ERR_INVALID_ARG, "null output");
+    const long long N = c->g.N;
+    if (N > noalloc_max_nodes())
+        return fail(c, LBE_ERR_UNSUPPORTED,
+                    "lbe_get_mass_noalloc: lattice of " + std::to_string(N) + " nodes exceeds its maximum of " +
+                        std::to_string(noalloc_max_nodes()) + " nodes");
+    double *scratch = nullptr;
+    CK(noalloc_scratch(c->device, &scratch), "lbe_get_mass_noalloc: device address of the scratch array");
+    LAUNCH(launch_mass_noalloc((int)c->prec, c->g.nx, c->g.ny, c->g.nz, c->pop[c->cur].p,
+                               (const uint32_t *)c->mask.p, c->M, c->n0, scratch, noalloc_blocks(N), c->stream),
+           "lbe_get_mass_noalloc kernels");
+    c->launches += 1;  // partial sums + final sum
+    CK(cudaMemcpyAsync(mass, scratch + noalloc_result_offset(), sizeof(double) * c->M, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "lbe_get_mass_noalloc: copy result");
+    CK(cudaStreamSynchronize(c->stream), "lbe_get_mass_noalloc: stream sync");
     return LBE_OK;
 }
 

@@ -84,6 +84,7 @@ def lib():
             "lbe_get_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
             "lbe_set_stage_timing": [_P, ctypes.c_int],
             "lbe_get_stage_times": [_P, _D, ctypes.POINTER(ctypes.c_longlong)],
+            "lbe_get_mass_noalloc": [_P, _D],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -322,6 +323,14 @@ def lbe_get_stage_times(ctx):
     n = (ctypes.c_longlong * 5)()
     _check(lib().lbe_get_stage_times(ctx, _dp(ms), n), ctx)
     return {STAGES[k]: (float(ms[k]), int(n[k])) for k in range(5)}
+
+
+def lbe_get_mass_noalloc(ctx, M):
+    """Species masses of the current state through the entry point that allocates no device memory
+    (for callers that cannot allocate at the time of the call; see include/lbe.h)."""
+    mass = np.zeros(M)
+    _check(lib().lbe_get_mass_noalloc(ctx, _dp(mass)), ctx)
+    return mass
 
 
 def lbe_status_string(status):
