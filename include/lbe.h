@@ -189,6 +189,22 @@ lbe_status lbe_get_link_mask(lbe_ctx *ctx, uint32_t *out);
  * as [k][3] ints into e (may be NULL) and the count into *count. */
 lbe_status lbe_shell(double sigma, int *e, int cap, int *count);
 
+/* Discrete adjoint (reverse mode through the whole step: streaming, DD-TR
+ * collision and moment recovery, mean-field shell force, contact values,
+ * density) of the time-averaged flux through a plane,
+ *   Phi = (1/T) sum_{t<T} sum_s sum_{plane fluid nodes} J^s_axis(t),
+ * over the next T = nsteps steps from the current state.  Outputs:
+ *   *Phi; dPhi_damp[N] = dPhi/da(r) for the wall-potential amplitude a(r)
+ *   (V^s += a(r) phi(r) for every species, lbe_set_wall_potential);
+ *   dPhi_dg[3] = dPhi/dg for a body force g added to every species.
+ * Checkpoints every ckpt_every steps are kept and each segment is recomputed
+ * in the reverse sweep (device memory: (T/ckpt_every + ckpt_every) copies of
+ * the populations).  FP64 and FP32 storage only (LBE_ERR_UNSUPPORTED for the
+ * 16-bit forms).  The state of the context is left as it was before the call;
+ * the flux time average is reset.  Any output pointer may be NULL. */
+lbe_status lbe_adjoint_flux_gradient(lbe_ctx *ctx, int nsteps, int ckpt_every, int axis, int plane,
+                                     double *dPhi_damp, double dPhi_dg[3], double *Phi);
+
 /* Stage timing: CUDA events recorded on the context stream around every kernel
  * launch of lbe_step.  on != 0 enables it and clears the totals; 0 disables it. */
 lbe_status lbe_set_stage_timing(lbe_ctx *ctx, int on);

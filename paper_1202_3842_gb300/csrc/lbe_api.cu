@@ -477,6 +477,27 @@ lbe_status state_moments(lbe_ctx *c, double **n, double **J) {
     return LBE_OK;
 }
 
+// One DD-TR step of the current populations (K1-K3, K4, and K5 when psize > 0).
+lbe_status step_once(lbe_ctx *c, const StepParams &sp, int psize) {
+    TRY(force_stage(c));
+    {
+        StageTimer tm(c, LBE_STAGE_COLLIDE);
+        LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
+                              c->solid_links, c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
+               "collide kernel");
+    }
+    c->cur = 1 - c->cur;
+    if (psize > 0) {
+        StageTimer tm(c, LBE_STAGE_FLUX);
+        LAUNCH(launch_flux_reduce(c->M, psize, (const double *)c->flux_buf.p, (double *)c->flux_acc.p,
+                                  (double *)c->flux_last.p, c->stream),
+               "flux reduction");
+        c->flux_count += 1;
+    }
+    c->steps += 1;
+    return LBE_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -701,23 +722,7 @@ lbe_status lbe_step(lbe_ctx *c, int nsteps) {
     const int psize = c->flux_plane >= 0 ? plane_size(c) : 0;
     if (psize > 0) TRY(dev_alloc(c, c->flux_buf, 8 * (size_t)c->M * psize));
     for (int t = 0; t < nsteps; ++t) {
-        TRY(force_stage(c));
-        {
-            StageTimer tm(c, LBE_STAGE_COLLIDE);
-            LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p,
-                                  (const uint32_t *)c->mask.p, c->solid_links, c->C.p, c->F.p, sp,
-                                  (double *)c->flux_buf.p, c->stream),
-                   "collide kernel");
-        }
-        c->cur = 1 - c->cur;
-        if (psize > 0) {
-            StageTimer tm(c, LBE_STAGE_FLUX);
-            LAUNCH(launch_flux_reduce(c->M, psize, (const double *)c->flux_buf.p, (double *)c->flux_acc.p,
-                                      (double *)c->flux_last.p, c->stream),
-                   "flux reduction");
-            c->flux_count += 1;
-        }
-        c->steps += 1;
+        TRY(step_once(c, sp, psize));
         c->steps_since_check += 1;
         if (c->cfg.check_every > 0 && c->steps_since_check >= c->cfg.check_every) {
             c->steps_since_check = 0;
@@ -952,6 +957,217 @@ lbe_status lbe_shell(double sigma, int *e, int cap, int *count) {
                 }
     *count = k;
     return LBE_OK;
+}
+
+lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int plane, double *dPhi_damp,
+                                     double dPhi_dg[3], double *Phi) {
+    TRY(ready(c));
+    if (T < 1 || K < 1) return fail(c, LBE_ERR_INVALID_ARG, "nsteps and ckpt_every must be >= 1");
+    if (axis < 0 || axis > 2) return fail(c, LBE_ERR_INVALID_ARG, "axis must be 0, 1 or 2");
+    const int extent = axis == 0 ? c->g.nx : (axis == 1 ? c->g.ny : c->g.nz);
+    if (plane < 0 || plane >= extent) return fail(c, LBE_ERR_INVALID_ARG, "plane index out of range");
+    if (!(c->prec == Prec::F32 || c->prec == Prec::F64))
+        return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint runs on FP64 or FP32 populations only");
+    TRY(prepare(c));
+    const bool f64 = prec_fp64(c->prec);
+    const size_t rb = real_bytes(c);
+    const long long N = c->g.N, P = c->g.P;
+    const int M = c->M;
+    const size_t pop_bytes = (size_t)prec_bytes(c->prec) * M * 2 * Q * N;
+    const int nseg = (T + K - 1) / K;
+    const int kseg = std::min(K, T);
+    const long long steps_before = c->steps;
+    const int old_axis = c->flux_axis, old_plane = c->flux_plane;
+
+    std::vector<Buf> ck(nseg), seg(kseg);
+    Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, hs, unit, outA, red;
+    auto release = [&]() {
+        for (auto &b : ck) dev_free(c, b);
+        for (auto &b : seg) dev_free(c, b);
+        Buf *all[] = {&lYf[0], &lYf[1], &lYg[0], &lYg[1], &lnd[0], &lnd[1], &lC, &lF, &lg, &Lpad, &gLpad,
+                      &lnbar, &hs, &unit, &outA, &red};
+        for (Buf *b : all) dev_free(c, *b);
+    };
+    auto alloc = [&](Buf &b, size_t bytes, bool zero) -> lbe_status {
+        lbe_status st = dev_alloc(c, b, bytes);
+        if (st != LBE_OK) return st;
+        if (zero && cudaMemsetAsync(b.p, 0, bytes, c->stream) != cudaSuccess)
+            return fail(c, LBE_ERR_CUDA, "memset of an adjoint buffer failed");
+        return LBE_OK;
+    };
+#define ATRY(x)                   \
+    do {                          \
+        lbe_status _s = (x);      \
+        if (_s != LBE_OK) {       \
+            release();            \
+            return _s;            \
+        }                         \
+    } while (0)
+    for (auto &b : ck) ATRY(alloc(b, pop_bytes, false));
+    for (auto &b : seg) ATRY(alloc(b, pop_bytes, false));
+    for (int k = 0; k < 2; ++k) {
+        ATRY(alloc(lYf[k], rb * M * Q * N, true));
+        ATRY(alloc(lYg[k], rb * M * Q * N, true));
+        ATRY(alloc(lnd[k], rb * M * N, true));
+    }
+    ATRY(alloc(lC, rb * M * 3 * N, true));
+    ATRY(alloc(lF, rb * M * 3 * N, true));
+    ATRY(alloc(lg, rb * M * M * N, true));
+    ATRY(alloc(Lpad, rb * 3 * P, true));
+    ATRY(alloc(gLpad, rb * 3 * P, true));
+    ATRY(alloc(lnbar, rb * M * P, true));
+    ATRY(alloc(outA, 8 * N, false));
+    ATRY(alloc(red, 8 * N, false));
+
+    // half-shell tables of every pair: padded offset, (ex, ey, ez), unit vectors
+    std::vector<int4> hs_h;
+    std::vector<double> unit_d;
+    std::vector<int> hs_start;
+    for (auto &ps : c->pairs) {
+        hs_start.push_back((int)hs_h.size());
+        const int S = ps.S;
+        for (int z = -S; z <= S; ++z)
+            for (int y = -S; y <= S; ++y)
+                for (int x = -S; x <= S; ++x)
+                    if (in_shell(S, x, y, z) && positive_half(x, y, z)) {
+                        const int off = x + c->g.px * (y + c->g.py * z);
+                        hs_h.push_back(make_int4(off, x, y, z));
+                        const double L = std::sqrt((double)(x * x + y * y + z * z));
+                        unit_d.push_back(x / L);
+                        unit_d.push_back(y / L);
+                        unit_d.push_back(z / L);
+                    }
+    }
+    hs_start.push_back((int)hs_h.size());
+    if (!hs_h.empty()) {
+        ATRY(alloc(hs, sizeof(int4) * hs_h.size(), false));
+        ATRY(alloc(unit, rb * unit_d.size(), false));
+        CK(cudaMemcpyAsync(hs.p, hs_h.data(), sizeof(int4) * hs_h.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy half shells");
+        if (f64) {
+            CK(cudaMemcpyAsync(unit.p, unit_d.data(), 8 * unit_d.size(), cudaMemcpyHostToDevice, c->stream),
+               "copy unit vectors");
+        } else {
+            std::vector<float> uf(unit_d.begin(), unit_d.end());
+            CK(cudaMemcpyAsync(unit.p, uf.data(), 4 * uf.size(), cudaMemcpyHostToDevice, c->stream),
+               "copy unit vectors");
+            CK(cudaStreamSynchronize(c->stream), "sync");
+        }
+    }
+
+    // forward sweep with checkpoints; the objective is the flux average of these T steps
+    c->flux_axis = axis;
+    c->flux_plane = plane;
+    c->flux_count = 0;
+    CK(cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream), "memset flux");
+    StepParams sp = step_params(c);
+    const int psize = plane_size(c);
+    ATRY(dev_alloc(c, c->flux_buf, 8 * (size_t)M * psize));
+    for (int s = 0; s < nseg; ++s) {
+        CK(cudaMemcpyAsync(ck[s].p, c->pop[c->cur].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+        const int nst = std::min(K, T - s * K);
+        for (int k = 0; k < nst; ++k) ATRY(step_once(c, sp, psize));
+    }
+    double acc[MAXS];
+    CK(cudaMemcpyAsync(acc, c->flux_acc.p, 8 * MAXS, cudaMemcpyDeviceToHost, c->stream), "copy flux");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    double phi_val = 0.0;
+    for (int a = 0; a < M; ++a) phi_val += acc[a];
+    phi_val /= (double)T;
+
+    // reverse sweep
+    AdjParams ap{};
+    ap.M = M;
+    ap.consistent = c->cfg.consistent_moments ? 1 : 0;
+    ap.axis = axis;
+    ap.plane = plane;
+    ap.wobj = 1.0 / (double)T;
+    for (int a = 0; a < M; ++a) ap.sp[a] = sp.sp[a];
+    StepParams sp0 = sp;
+    sp0.flux_axis = -1;
+    int cl = 0;
+    for (int s = nseg - 1; s >= 0; --s) {
+        const int nst = std::min(K, T - s * K);
+        CK(cudaMemcpyAsync(c->pop[c->cur].p, ck[s].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "restore");
+        for (int k = 0; k < nst; ++k) {
+            CK(cudaMemcpyAsync(seg[k].p, c->pop[c->cur].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "save");
+            ATRY(step_once(c, sp0, 0));
+        }
+        for (int k = nst - 1; k >= 0; --k) {
+            CK(cudaMemcpyAsync(c->pop[c->cur].p, seg[k].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream),
+               "restore step");
+            ATRY(force_stage(c));
+            LAUNCH(launch_adj_collide(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p,
+                                      ap, lYf[cl].p, lYg[cl].p, lnd[cl].p, lYf[1 - cl].p, lYg[1 - cl].p, lC.p,
+                                      lF.p, c->stream),
+                   "adjoint collide");
+            CK(cudaMemsetAsync(lnd[1 - cl].p, 0, rb * M * N, c->stream), "memset");
+            CK(cudaMemsetAsync(lg.p, 0, rb * M * M * N, c->stream), "memset");
+            for (size_t q = 0; q < c->pairs.size(); ++q) {
+                const auto &ps = c->pairs[q];
+                AdjShell L{};
+                L.hs = (const int4 *)hs.p + hs_start[q];
+                L.unit = (const char *)unit.p + rb * 3 * hs_start[q];
+                L.nhalf = hs_start[q + 1] - hs_start[q];
+                L.npad_a = (const char *)c->npad.p + rb * ps.a * P;
+                L.npad_b = (const char *)c->npad.p + rb * ps.b * P;
+                L.gnpad = (const char *)c->gnpad.p + rb * (ps.a * M + ps.b) * P;
+                L.gab = (const char *)c->gab.p + rb * (ps.a * M + ps.b) * N;
+                L.lC_a = (const char *)lC.p + rb * 3 * ps.a * N;
+                L.Lpad = Lpad.p;
+                L.gLpad = gLpad.p;
+                L.coef = ps.coef;
+                L.ln = lnd[1 - cl].p;
+                L.lg = (char *)lg.p + rb * (ps.a * M + ps.b) * N;
+                L.a = ps.a;
+                L.b = ps.b;
+                LAUNCH(launch_adj_shell(f64, c->g, L, c->stream), "adjoint shell");
+                c->launches += 1;
+            }
+            if (!c->pairs.empty()) {
+                LAUNCH(launch_adj_contact(f64, c->g, c->cparams, c->brows, (const uint32_t *)c->mask.p, c->npad.p,
+                                          lg.p, lnbar.p, lnd[1 - cl].p, c->stream),
+                       "adjoint contact");
+                c->launches += 1;
+            }
+            cl = 1 - cl;
+        }
+    }
+
+    // dPhi/damp and dPhi/dg
+    if (dPhi_damp) {
+        LAUNCH(launch_adj_amp(f64, c->g, M, lF.p, (const double *)c->phi.p, (double *)outA.p, c->stream),
+               "adjoint amplitude");
+        CK(cudaMemcpyAsync(dPhi_damp, outA.p, 8 * N, cudaMemcpyDeviceToHost, c->stream), "copy gradient");
+    }
+    if (dPhi_dg) {
+        for (int k = 0; k < 3; ++k) {
+            double tot = 0.0, r2[2];
+            for (int a = 0; a < M; ++a) {
+                LAUNCH(launch_to_f64(f64, (const char *)lF.p + rb * (3 * a + k) * N, N, (double *)red.p, c->stream),
+                       "convert");
+                LAUNCH(launch_reduce((const double *)red.p, N, (double *)c->partial.p, 1024, (double *)c->red_out.p,
+                                     c->stream),
+                       "reduce");
+                CK(cudaMemcpyAsync(r2, c->red_out.p, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+                CK(cudaStreamSynchronize(c->stream), "sync");
+                tot += r2[0];
+            }
+            dPhi_dg[k] = tot;
+        }
+    }
+    if (Phi) *Phi = phi_val;
+    // leave the state as it was
+    CK(cudaMemcpyAsync(c->pop[c->cur].p, ck[0].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "restore state");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    c->steps = steps_before;
+    c->flux_axis = old_axis;
+    c->flux_plane = old_plane;
+    c->flux_count = 0;
+    CK(cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream), "memset flux");
+    release();
+#undef ATRY
+    return check_error_word(c);
 }
 
 lbe_status lbe_set_stage_timing(lbe_ctx *c, int on) {

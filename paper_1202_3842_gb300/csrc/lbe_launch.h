@@ -115,4 +115,39 @@ cudaError_t launch_to_f64(bool fp64, const void *src, long long n, double *dst, 
 // Copy the interior of a padded field to a dense FP64 array.
 cudaError_t launch_unpad(bool fp64, const Grid &g, const void *pad, double *dst, cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// discrete adjoint (lbe_adjoint.cu)
+// ---------------------------------------------------------------------------
+struct AdjParams {
+    int M;
+    int consistent;
+    int axis;     // flux plane
+    int plane;
+    double wobj;  // weight of one step's flux in the objective (1/T)
+    SpeciesConst sp[MAXS];
+};
+
+struct AdjShell {
+    const int4 *hs;    // half shell: padded offset, ex, ey, ez
+    const void *unit;  // unit vectors [nhalf][3] (compute precision)
+    int nhalf;
+    const void *npad_a, *npad_b, *gnpad, *gab, *lC_a;
+    void *Lpad, *gLpad;  // [3][P] work fields
+    double coef;
+    void *ln;  // [M][N] density adjoint (accumulated)
+    void *lg;  // [N] contact-value adjoint of this pair (accumulated)
+    int a, b;
+};
+
+cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const uint32_t *mask, const void *C,
+                               const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
+                               const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF,
+                               cudaStream_t st);
+cudaError_t launch_adj_shell(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st);
+cudaError_t launch_adj_contact(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
+                               const uint32_t *mask, const void *npad, const void *lg, void *lnbar, void *ln,
+                               cudaStream_t st);
+cudaError_t launch_adj_amp(bool fp64, const Grid &g, int M, const void *lF, const double *phi, double *out,
+                           cudaStream_t st);
+
 }  // namespace lbe

@@ -85,6 +85,7 @@ def lib():
             "lbe_set_stage_timing": [_P, ctypes.c_int],
             "lbe_get_stage_times": [_P, _D, ctypes.POINTER(ctypes.c_longlong)],
             "lbe_get_mass_noalloc": [_P, _D],
+            "lbe_adjoint_flux_gradient": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -333,6 +334,16 @@ def lbe_get_mass_noalloc(ctx, M):
     return mass
 
 
+def lbe_adjoint_flux_gradient(ctx, N, nsteps, ckpt_every, axis, plane):
+    """(Phi, dPhi/damp [N], dPhi/dg [3]) of the flux averaged over the next nsteps steps (state unchanged)."""
+    dA = np.zeros(N)
+    dg = np.zeros(3)
+    phi = ctypes.c_double(0.0)
+    _check(lib().lbe_adjoint_flux_gradient(ctx, int(nsteps), int(ckpt_every), int(axis), int(plane), _dp(dA),
+                                           _dp(dg), ctypes.byref(phi)), ctx)
+    return phi.value, dA, dg
+
+
 def lbe_status_string(status):
     return lib().lbe_status_string(int(status)).decode()
 
@@ -434,6 +445,9 @@ class Simulation:
 
     def launch_count(self):
         return lbe_get_launch_count(self._h)
+
+    def adjoint_flux_gradient(self, nsteps, ckpt_every, axis, plane):
+        return lbe_adjoint_flux_gradient(self._h, self.N, nsteps, ckpt_every, axis, plane)
 
     def set_stage_timing(self, on):
         lbe_set_stage_timing(self._h, on)

@@ -1,0 +1,124 @@
+"""GPU discrete adjoint of the time-averaged flux against the FP64 reference gradient (autograd through
+an independent FP64 implementation of the step, itself pinned to the C oracle) and against central finite
+differences of the GPU FP64 forward.
+
+Tolerances: FP64 adjoint vs reference 1e-10 of the largest gradient entry; FP64 adjoint vs central
+differences (h = 1e-4 of the parameter scale) 1e-6 relative; FP32 adjoint vs FP64 reference 1e-3 of the
+largest entry."""
+import numpy as np
+import pytest
+
+from lbe_cases import setup_gpu
+from paper_1202_3842_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+KT = 1.0 / 3.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    from paper_1202_3842_gb300 import build
+    build.build()
+
+
+def _case(shape=(16, 12, 10), sig=(2.0, 4.0), taus=(1.0, 0.9), width=6, length=4, body=2e-4, seed=21):
+    w = inputs.channel_workload(shape, sig, 0.2, taus, width, length, body=body, wall_amp_kT=1.0)
+    arr = inputs.build_workload(w)
+    rng = np.random.default_rng(seed)
+    arr["amp"] = arr["amp"] * (1.0 + 0.3 * (rng.random(arr["amp"].size) - 0.5))
+    return w, arr
+
+
+def _reference(w, arr, T, axis, plane, consistent=False):
+    from oracle import torch_adjoint
+    return torch_adjoint.reference_gradient(w["shape"], w["periodic"], w["sigma"], w["tau"], arr["solid"],
+                                            arr["phi"], arr["V"], w["body"], arr["n"], arr["amp"], T, axis, plane,
+                                            consistent=consistent)
+
+
+@pytest.mark.parametrize("consistent", [False, True])
+def test_fp64_adjoint_matches_reference(consistent):
+    w, arr = _case()
+    T, axis, plane = 8, 0, 8
+    g = setup_gpu(w, arr, "fp64", consistent=consistent)
+    f0, g0 = g.populations(0)
+    Phi, dA, dG = g.adjoint_flux_gradient(T, 3, axis, plane)
+    rPhi, rA, rG = _reference(w, arr, T, axis, plane, consistent)
+    assert abs(Phi - rPhi) <= 1e-12 * abs(rPhi)
+    assert np.abs(dA - rA).max() <= 1e-10 * np.abs(rA).max()
+    assert np.abs(dG - rG).max() <= 1e-10 * np.abs(rG).max()
+    f1, g1 = g.populations(0)  # the state is left as it was
+    np.testing.assert_array_equal(f1, f0)
+    np.testing.assert_array_equal(g1, g0)
+
+
+def _gpu_phi(w, arr, amp, gshift, T, axis, plane, prec="fp64"):
+    a2 = dict(arr)
+    a2["amp"] = amp
+    w2 = dict(w)
+    w2["body"] = [tuple(np.asarray(b) + gshift) for b in w["body"]]
+    g = setup_gpu(w2, a2, prec)
+    g.set_flux_plane(axis, plane)
+    g.step(T)
+    return g.flux(-1)[1]
+
+
+def test_fp64_adjoint_matches_central_differences_of_the_gpu_forward():
+    w, arr = _case(shape=(24, 14, 12), sig=(4.0, 6.0), taus=(1.0, 1.0), width=8, length=6, seed=3)
+    T, axis, plane = 30, 0, 12
+    g = setup_gpu(w, arr, "fp64")
+    Phi, dA, dG = g.adjoint_flux_gradient(T, 7, axis, plane)
+    rng = np.random.default_rng(4)
+    N = arr["amp"].size
+    wall = np.flatnonzero(arr["phi"] > 0)
+    dirs = [rng.standard_normal(N) * (arr["phi"] > 0) for _ in range(2)]
+    for node in wall[[3, len(wall) // 3, -5]]:
+        d = np.zeros(N)
+        d[node] = 1.0
+        dirs.append(d)
+    h = 1e-4 * KT
+    for d in dirs:
+        fp = _gpu_phi(w, arr, arr["amp"] + h * d, np.zeros(3), T, axis, plane)
+        fm = _gpu_phi(w, arr, arr["amp"] - h * d, np.zeros(3), T, axis, plane)
+        fd = (fp - fm) / (2 * h)
+        ad = float(dA @ d)
+        assert abs(ad - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(dA).max()), (ad, fd)
+    hg = 1e-4 * 2e-4
+    e = np.array([hg, 0.0, 0.0])
+    fd = (_gpu_phi(w, arr, arr["amp"], e, T, axis, plane) - _gpu_phi(w, arr, arr["amp"], -e, T, axis, plane)) / (2 * hg)
+    assert abs(dG[0] - fd) <= 1e-6 * abs(fd)
+
+
+def test_fp32_adjoint_against_fp64_reference_channel32():
+    w = inputs.WORKLOADS["channel32adj"]()
+    arr = inputs.build_workload(w)
+    rng = np.random.default_rng(7)
+    arr["amp"] = arr["amp"] * (1.0 + 0.3 * (rng.random(arr["amp"].size) - 0.5))
+    T, axis, plane = 200, 0, 16
+    g = setup_gpu(w, arr, "fp32")
+    Phi, dA, dG = g.adjoint_flux_gradient(T, 20, axis, plane)
+    from oracle import torch_adjoint
+    rPhi, rA, rG = torch_adjoint.reference_gradient(w["shape"], w["periodic"], w["sigma"], w["tau"], arr["solid"],
+                                                    arr["phi"], arr["V"], w["body"], arr["n"], arr["amp"], T, axis,
+                                                    plane, ckpt_every=1)
+    assert abs(Phi - rPhi) <= 1e-3 * abs(rPhi)
+    assert np.abs(dA - rA).max() <= 1e-3 * np.abs(rA).max()
+    assert np.abs(dG - rG).max() <= 1e-3 * np.abs(rG).max()
+
+
+def test_autograd_function_returns_the_adjoint_gradient():
+    from paper_1202_3842_gb300.autograd import FluxObjective
+    w, arr = _case()
+    T, axis, plane = 8, 0, 8
+    g = setup_gpu(w, arr, "fp64")
+    amp = torch.tensor(arr["amp"], dtype=torch.float64, requires_grad=True)
+    gs = torch.zeros(3, dtype=torch.float64, requires_grad=True)
+    Phi = FluxObjective.apply(amp, gs, g, arr["phi"], w["body"], arr["n"], T, 4, axis, plane)
+    (2.0 * Phi).backward()
+    rPhi, rA, rG = _reference(w, arr, T, axis, plane)
+    assert abs(float(Phi) - rPhi) <= 1e-12 * abs(rPhi)
+    assert np.abs(amp.grad.numpy() - 2 * rA).max() <= 1e-10 * np.abs(rA).max()
+    assert np.abs(gs.grad.numpy() - 2 * rG).max() <= 1e-10 * np.abs(rG).max()
