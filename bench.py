@@ -69,7 +69,10 @@ def parse():
     p.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "bf16", "fp16"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--no-extra", action="store_true", help="skip the bounded spherical-well line")
+    p.add_argument("--no-extra", action="store_true", help="skip the bounded spherical-well and adjoint lines")
+    p.add_argument("--adjoint-only", action="store_true", help="time only the adjoint against the forward")
+    p.add_argument("--adjoint-steps", type=int, default=2000)
+    p.add_argument("--adjoint-ckpt", type=int, default=100)
     return p.parse_args()
 
 
@@ -414,6 +417,44 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     return res, w, arrays
 
 
+def measure_adjoint(prec, wname="channel256adj", T=2000, K=100):
+    """Adjoint / forward time: T forward steps with the flux accumulation, against lbe_adjoint_flux_gradient
+    over the same T steps (forward sweep with checkpoints every K steps, segment recomputation, reverse sweep),
+    both wall clock with the stream synchronised, from the same initial state."""
+    import torch
+    from paper_1202_3842_gb300 import inputs
+    w = inputs.WORKLOADS[wname]()
+    arrays = inputs.build_workload(w)
+    M = len(w["sigma"])
+    sim = make_sim(w, arrays, prec)
+    sim.step(3)
+    plane = w["shape"][0] // 2
+    for a in range(M):
+        sim.init_density(a, arrays["n"][a])
+    sim.set_flux_plane(0, plane)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(T)
+    phi_fwd = sim.flux(-1)[1]
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    for a in range(M):
+        sim.init_density(a, arrays["n"][a])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi, dA, dG = sim.adjoint_flux_gradient(T, K, 0, plane)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "steps": T,
+            "ckpt_every": K, "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_fwd,
+            "Phi": phi, "Phi_forward_check": phi_fwd, "dPhi_dg": list(dG), "max_abs_dPhi_damp": float(abs(dA).max()),
+            "what": "gradient of the flux through x = nx/2 averaged over the steps, w.r.t. the per-node wall-potential "
+                    "amplitude and the body force"}
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -427,6 +468,9 @@ def run_ours(args):
 
     from paper_1202_3842_gb300 import build, lbe
     build.build()
+    if args.adjoint_only:
+        print(json.dumps({"adjoint": measure_adjoint(args.prec, T=args.adjoint_steps, K=args.adjoint_ckpt)}))
+        return 0
     peaks, peaks_kind = load_peaks()
     core, w, arrays = measure(args, args.workload, args.prec, args.steps, args.warmup, dist, world, local, peaks,
                               peaks_kind, sampler=ClockSampler(local))
@@ -477,6 +521,9 @@ def run_ours(args):
                          "recovery as printed diverges after about a hundred steps at this packing and well "
                          "depth (oracle and GPU agree), so no longer window is physical" % (5 + k))
         result["well256_bounded"] = extra
+
+    if not args.no_extra and args.prec in ("fp32", "fp64"):
+        result["adjoint"] = measure_adjoint(args.prec, T=args.adjoint_steps, K=args.adjoint_ckpt)
 
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, arrays)

@@ -12,11 +12,15 @@ __device__ __forceinline__ long long pop_off(int a, int fg, int p, long long N) 
     return ((long long)(a * 2 + fg) * Q + p) * N;
 }
 
+// Lattices hold fewer than 2^31 nodes (checked at creation), so 32-bit
+// division suffices.
 __device__ __forceinline__ void node_xyz(const Grid &g, long long i, int &x, int &y, int &z) {
-    x = (int)(i % g.nx);
-    long long r = i / g.nx;
-    y = (int)(r % g.ny);
-    z = (int)(r / g.ny);
+    const unsigned ii = (unsigned)i, nx = (unsigned)g.nx, ny = (unsigned)g.ny;
+    const unsigned r = ii / nx;
+    x = (int)(ii - r * nx);
+    const unsigned q = r / ny;
+    y = (int)(r - q * ny);
+    z = (int)q;
 }
 
 // Linear offsets to the six neighbours with periodic wrap (a closed axis wraps

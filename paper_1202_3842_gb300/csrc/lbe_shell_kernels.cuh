@@ -290,6 +290,18 @@ __global__ void __launch_bounds__(32 * TYB, 1)
         for (int j = j0; j < j0 + NK; ++j)
             if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
         if (active) {
+            // the epilogue's global loads are issued before the shell sum so their latency hides behind it
+            T na[TZ], gr[TZ], old[TZ][3];
+            long long idx[TZ];
+#pragma unroll
+            for (int t = 0; t < TZ; ++t) {
+                const int z = min(z0 + j0 + t, zend - 1);
+                idx[t] = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+                na[t] = npad_a[pidx(g, x, y, z)];
+                gr[t] = g_ab[idx[t]];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) old[t][c] = accumulate ? Cout[(long long)c * g.N + idx[t]] : (T)0;
+            }
             const T *sb[NK];
 #pragma unroll
             for (int k = 0; k < NK; ++k) sb[k] = ring + ((j0 + k) % Tl::R) * SLOT + toff;
@@ -310,21 +322,11 @@ __global__ void __launch_bounds__(32 * TYB, 1)
             all_columns<T, S, TZ, TYB>(sb, an, ag, std::make_integer_sequence<int, ColTable<S>::count>{});
 #pragma unroll
             for (int t = 0; t < TZ; ++t) {
-                const int z = z0 + j0 + t;
-                if (z < zend) {
-                    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-                    const T na = npad_a[pidx(g, x, y, z)];
-                    const T gr = g_ab[i];
-                    const T pre = coef * na;
+                if (z0 + j0 + t < zend) {
+                    const T pre = coef * na[t];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const T v = pre * (half * gr * an[t][c] + half * ag[t][c]);
-                        T *o = Cout + (long long)c * g.N + i;
-                        if (accumulate)
-                            *o += v;
-                        else
-                            *o = v;
-                    }
+                    for (int c = 0; c < 3; ++c)
+                        Cout[(long long)c * g.N + idx[t]] = old[t][c] + pre * (half * gr[t] * an[t][c] + half * ag[t][c]);
                 }
             }
         }
