@@ -178,10 +178,12 @@ def source_hash(files):
 
 
 KERNEL_SOURCES = {
-    "collide": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "collide": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh",
+                "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
     "shell": ["paper_1202_3842_gb300/csrc/lbe_shell.cu", "paper_1202_3842_gb300/csrc/lbe_shell.cuh",
               "paper_1202_3842_gb300/csrc/lbe_shell_kernels.cuh", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
-    "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
+    "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh",
+                "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
     "contact": ["paper_1202_3842_gb300/csrc/lbe_contact.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "flux": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu"],
 }
