@@ -180,6 +180,31 @@ lbe_status lbe_set_populations(lbe_ctx *ctx, int s, const double *f, const doubl
 /* Number of steps taken since lbe_init_density / lbe_set_populations. */
 lbe_status lbe_get_step_count(lbe_ctx *ctx, long long *steps);
 
+/* Checkpoint and restart of the state: the populations in their storage
+ * precision, the reference densities n0 of the shifted 16-bit storage, the
+ * step count, the flux plane and its accumulators.  The lattice geometry,
+ * species, potentials and body forces are not part of it; a context that loads
+ * a state is given the same ones through their own calls.
+ * lbe_save_state: with host_buf NULL, *bytes receives the size of the state;
+ * otherwise host_buf (caller-owned, *bytes bytes) receives the state and
+ * *bytes its size (LBE_ERR_INVALID_ARG if *bytes is too small).  Synchronises.
+ * lbe_load_state: LBE_ERR_INVALID_ARG if the buffer does not hold a state of
+ * this library with the context's lattice size, species count and precision;
+ * the context is unchanged then.  A state saved and loaded continues
+ * bit-identically to the run it was saved from. */
+lbe_status lbe_save_state(lbe_ctx *ctx, void *host_buf, size_t *bytes);
+lbe_status lbe_load_state(lbe_ctx *ctx, const void *host_buf, size_t bytes);
+
+/* Steady-state residual (the criterion of a run to steady state):
+ *   *res = max over species s and nodes r of |n^s(r,t) - n^s(r,t0)| / ((t - t0) n0^s),
+ * t the current step count, t0 the step count at the previous call and n0^s the
+ * reference density of species s (the fluid-node mean of its last
+ * lbe_init_density; 1 if none was given).  Every call records the current
+ * densities for the next one; the first call after lbe_create,
+ * lbe_init_density, lbe_set_populations or lbe_load_state, and a call with
+ * t = t0, only record them and return *res = -1.  FP64; synchronises. */
+lbe_status lbe_get_residual(lbe_ctx *ctx, double *res);
+
 /* Per-node blocked-link mask (bit p set: the population arriving along c_p
  * comes from a solid node or from outside a closed axis), out[N]. */
 lbe_status lbe_get_link_mask(lbe_ctx *ctx, uint32_t *out);
@@ -197,10 +222,12 @@ lbe_status lbe_shell(double sigma, int *e, int cap, int *count);
  *   *Phi; dPhi_damp[N] = dPhi/da(r) for the wall-potential amplitude a(r)
  *   (V^s += a(r) phi(r) for every species, lbe_set_wall_potential);
  *   dPhi_dg[3] = dPhi/dg for a body force g added to every species.
- * Checkpoints every ckpt_every steps are kept and each segment is recomputed
- * in the reverse sweep (device memory: (T/ckpt_every + ckpt_every) copies of
- * the populations).  FP64 and FP32 storage only (LBE_ERR_UNSUPPORTED for the
- * 16-bit forms).  The state of the context is left as it was before the call;
+ * Checkpoints every K = ckpt_every steps are kept and each segment is
+ * recomputed in the reverse sweep, keeping the states of the segment and the
+ * fields of their force stages (device memory: ceil(T/K) + K - 1 copies of the
+ * populations, plus for each of the K steps M^2 + 3 M + 3 npairs words per
+ * node and M (M + 1) words per node of the padded lattice).  FP64 and FP32 storage only
+ * (LBE_ERR_UNSUPPORTED for the 16-bit forms).  The state of the context is left as it was before the call;
  * the flux time average is reset.  Any output pointer may be NULL. */
 lbe_status lbe_adjoint_flux_gradient(lbe_ctx *ctx, int nsteps, int ckpt_every, int axis, int plane,
                                      double *dPhi_damp, double dPhi_dg[3], double *Phi);

@@ -1,0 +1,10 @@
+// Explicit instantiations of the shell-transpose kernels (adjoint of K3), one group per
+// translation unit so that the builds run in parallel.
+#include "lbe_adj_shell.cuh"
+
+namespace lbe {
+template cudaError_t launch_adj_tile<float, 1, 2, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<float, 2, 2, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<float, 3, 2, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<float, 4, 2, 16>(const AdjShellTile &, cudaStream_t);
+}  // namespace lbe

@@ -1,0 +1,7 @@
+// Explicit instantiations of the shell-transpose kernels (adjoint of K3), one group per
+// translation unit so that the builds run in parallel.
+#include "lbe_adj_shell.cuh"
+
+namespace lbe {
+template cudaError_t launch_adj_tile<float, 8, 1, 8>(const AdjShellTile &, cudaStream_t);
+}  // namespace lbe

@@ -1,0 +1,11 @@
+// Explicit instantiations of the shell-transpose kernels (adjoint of K3), one group per
+// translation unit so that the builds run in parallel.
+#include "lbe_adj_shell.cuh"
+
+namespace lbe {
+template cudaError_t launch_adj_tile<double, 1, 1, 8>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<double, 2, 1, 8>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<double, 3, 1, 8>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<double, 4, 1, 8>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile<double, 5, 1, 4>(const AdjShellTile &, cudaStream_t);
+}  // namespace lbe

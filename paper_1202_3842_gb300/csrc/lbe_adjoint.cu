@@ -6,8 +6,11 @@
 // of the streamed populations at t+1 and produces the adjoint at t:
 //   K4^T  k_adj_collide   streaming transpose (push-gather), collision and moment
 //                         recovery transposed node by node; emits lambda_C, adds lambda_F
-//   K3^T  k_adj_shell_prep / k_adj_shell   shell force transposed: a divergence-type
-//                         shell sum of the weighted adjoint, plus the own-node terms
+//                         and the adjoint moments (ln, lPi, lJ) of each species;
+//         k_adj_write     the adjoint of the pre-collision populations from them
+//   K3^T  k_adj_shell_prep / k_adj_shell_tile   shell force transposed: node-local
+//                         terms, then divergence-type shell sums of the weighted
+//                         adjoint from shared-memory tiles (lbe_adj_shell.cuh)
 //   K2^T  k_adj_contact_prep / k_adj_ball  BMCSL contact value and ball average transposed
 //   K1^T  the density adjoint is kept as a field and added in the next push-gather
 // All arithmetic in the precision T of the populations (FP32 or FP64).
@@ -20,6 +23,7 @@
 namespace lbe {
 
 constexpr int ANT = 256;
+constexpr int ACT = 256;  // k_adj_collide: two CTAs per SM (FP32: 128 registers), one (FP64)
 
 // Adjoint of the post-collision population p of species a at node i, gathered
 // from the adjoint of the streamed populations at t+1 (the streaming is a
@@ -38,24 +42,18 @@ __device__ __forceinline__ T gather_post(const T *__restrict__ lY, const T *__re
 }
 
 template <typename S, typename T, int M>
-__global__ void __launch_bounds__(ANT, 1)
+__global__ void __launch_bounds__(ACT, sizeof(T) == 4 ? 2 : 1)
     k_adj_collide(Grid g, const S *__restrict__ post, const uint32_t *__restrict__ mask, const T *__restrict__ C,
                   const T *__restrict__ F, AdjParams ap, const T *__restrict__ lYf_in, const T *__restrict__ lYg_in,
-                  const T *__restrict__ lnd_in, T *__restrict__ lYf_out, T *__restrict__ lYg_out,
-                  T *__restrict__ lC, T *__restrict__ lF) {
+                  const T *__restrict__ lnd_in, T *__restrict__ lmom, T *__restrict__ lC, T *__restrict__ lF) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
     const uint32_t m = mask[i];
     if (m & 1u) {
-        for (int a = 0; a < M; ++a) {
-            for (int p = 0; p < Q; ++p) {
-                lYf_out[((long long)a * Q + p) * g.N + i] = (T)0;
-                lYg_out[((long long)a * Q + p) * g.N + i] = (T)0;
-            }
+        for (int a = 0; a < M; ++a)
             for (int c = 0; c < 3; ++c) lC[((long long)a * 3 + c) * g.N + i] = (T)0;
-        }
         return;
     }
     const NbrOff o = nbr_offsets(g, x, y, z);
@@ -220,92 +218,94 @@ __global__ void __launch_bounds__(ANT, 1)
             lF[((long long)a * 3 + c) * g.N + i] += n[a] * lnF[c];
             lC[((long long)a * 3 + c) * g.N + i] = lCv[c];
         }
-        const T *lYf = lYf_in + (long long)a * Q * g.N;
-        const T *lYg = lYg_in + (long long)a * Q * g.N;
-        const T *lnd = lnd_in + (long long)a * g.N;
-        T *of = lYf_out + (long long)a * Q * g.N + i;
-        T *og = lYg_out + (long long)a * Q * g.N + i;
-        [&]<int... P>(std::integer_sequence<int, P...>) {
-            (
-                [&] {
-                    const T lfs = gather_post<T, P>(lYf, lnd, g.N, i, o, m);
-                    const T lgs = gather_post<T, P>(lYg, nullptr, g.N, i, o, m);
-                    of[(long long)P * g.N] = ((T)1 - om) * lfs + ln;
-                    og[(long long)P * g.N] = ((T)1 - om) * lgs + lPit + cdot<T, P>(lJ);
-                }(),
-                ...);
-        }(std::make_integer_sequence<int, Q>{});
+        // adjoint moments of the pre-collision populations, for k_adj_write
+        T *lm = lmom + (long long)a * 5 * g.N + i;
+        lm[0] = ln;
+        lm[g.N] = lPit;
+        lm[2 * g.N] = lJ[0];
+        lm[3 * g.N] = lJ[1];
+        lm[4 * g.N] = lJ[2];
     }
 }
 
+// Adjoint of the pre-collision populations of species a = blockIdx.y at time t:
+//   lf_p = (1 - omega_eff) lf*_p + ln,   lg_p = (1 - omega_eff) lg*_p + lPi + c_p.lJ,
+// lf*_p, lg*_p the push-gathered adjoint of the post-collision populations (density adjoint added
+// to f) and (ln, lPi, lJ) the adjoint moments from k_adj_collide.  Zero on solid nodes.
+template <typename T>
+__global__ void __launch_bounds__(ANT)
+    k_adj_write(Grid g, const uint32_t *__restrict__ mask, AdjParams ap, const T *__restrict__ lYf_in,
+                const T *__restrict__ lYg_in, const T *__restrict__ lnd_in, const T *__restrict__ lmom,
+                T *__restrict__ lYf_out, T *__restrict__ lYg_out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.N) return;
+    const int a = blockIdx.y;
+    T *of = lYf_out + (long long)a * Q * g.N + i;
+    T *og = lYg_out + (long long)a * Q * g.N + i;
+    const uint32_t m = mask[i];
+    if (m & 1u) {
+#pragma unroll
+        for (int p = 0; p < Q; ++p) {
+            of[(long long)p * g.N] = (T)0;
+            og[(long long)p * g.N] = (T)0;
+        }
+        return;
+    }
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const NbrOff o = nbr_offsets(g, x, y, z);
+    const T om1 = (T)1 - (T)ap.sp[a].omega_eff;
+    const T *lm = lmom + (long long)a * 5 * g.N + i;
+    const T ln = lm[0], lPit = lm[g.N];
+    const T lJ[3] = {lm[2 * g.N], lm[3 * g.N], lm[4 * g.N]};
+    const T *lYf = lYf_in + (long long)a * Q * g.N;
+    const T *lYg = lYg_in + (long long)a * Q * g.N;
+    const T *lnd = lnd_in + (long long)a * g.N;
+    [&]<int... P>(std::integer_sequence<int, P...>) {
+        (
+            [&] {
+                const T lfs = gather_post<T, P>(lYf, lnd, g.N, i, o, m);
+                const T lgs = gather_post<T, P>(lYg, nullptr, g.N, i, o, m);
+                of[(long long)P * g.N] = om1 * lfs + ln;
+                og[(long long)P * g.N] = om1 * lgs + lPit + cdot<T, P>(lJ);
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, Q>{});
+}
+
 // ---------------------------------------------------------------------------
-// Shell force transposed, pair (a, b):  C^a += coef n_a [g/2 P + Q/2] with
-// P = sum_e e^ n_b(r+e), Q = sum_e e^ (g n_b)(r+e).  With Lambda = coef n_a lC^a / 2:
-//   ln_b(s) += -sum_e e^.(g Lambda)(s+e) - g(s) sum_e e^.Lambda(s+e)
-//   lg(s)   += -n_b(s) sum_e e^.Lambda(s+e) + Lambda(s).P(s)
-//   ln_a(s) += coef/2 (g(s) P(s) + Q(s)).lC^a(s)
+// Shell force transposed, pair (a, b), node-local part.  C^a += coef n_a
+// [g/2 P + Q/2] with P = sum_e e^ n_b(r+e), Q = sum_e e^ (g n_b)(r+e).  With
+// Lambda = coef n_a lC^a / 2 this kernel writes the padded fields Lambda and
+// g Lambda (read by the shell sums of lbe_adj_shell.cuh) and adds
+//   lg(s)   += Lambda(s).P(s),
+//   ln_a(s) += C^a(s).lC^a(s) / n_a(s)      (own = 1: once per species a;
+// summed over b, coef/2 (g P + Q).lC^a is C^a.lC^a / n_a).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_adj_shell_prep(Grid g, const T *__restrict__ npad_a, const T *__restrict__ gab,
-                                 const T *__restrict__ lC_a, T coef, T *__restrict__ Lpad, T *__restrict__ gLpad) {
+                                 const T *__restrict__ lC_a, const T *__restrict__ P, const T *__restrict__ C_a,
+                                 T coef, int own, T *__restrict__ Lpad, T *__restrict__ gLpad, T *__restrict__ ln_a,
+                                 T *__restrict__ lg) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
-    const T s = (T)0.5 * coef * npad_a[pidx(g, x, y, z)];
+    const T na = npad_a[pidx(g, x, y, z)];
+    const T s = (T)0.5 * coef * na;
     const T gv = gab[i];
+    T lp = 0, cl = 0;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const T L = s * lC_a[(long long)c * g.N + i];
+        const T lc = lC_a[(long long)c * g.N + i];
+        const T L = s * lc;
         write_padded<T>(g, Lpad + (long long)c * g.P, x, y, z, L);
         write_padded<T>(g, gLpad + (long long)c * g.P, x, y, z, gv * L);
+        lp += L * P[(long long)c * g.N + i];
+        cl += C_a[(long long)c * g.N + i] * lc;
     }
-}
-
-template <typename T>
-__global__ void __launch_bounds__(ANT)
-    k_adj_shell(Grid g, int nhalf, const int4 *__restrict__ hs /* padded offset, ex, ey, ez */,
-                const T *__restrict__ ux /* unit vectors [nhalf][3] */, const T *__restrict__ npad_a,
-                const T *__restrict__ npad_b, const T *__restrict__ gnpad, const T *__restrict__ gab,
-                const T *__restrict__ lC_a, const T *__restrict__ Lpad, const T *__restrict__ gLpad, T coef,
-                int same, T *__restrict__ ln, int a, int b, T *__restrict__ lg) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
-    int x, y, z;
-    node_xyz(g, i, x, y, z);
-    const long long pc = pidx(g, x, y, z);
-    T Pv[3] = {0, 0, 0}, Qv[3] = {0, 0, 0}, TP = 0, TQ = 0;
-    for (int k = 0; k < nhalf; ++k) {
-        const long long off = hs[k].x;
-        const T e0 = ux[3 * k], e1 = ux[3 * k + 1], e2 = ux[3 * k + 2];
-        const T dn = __ldg(npad_b + pc + off) - __ldg(npad_b + pc - off);
-        const T dq = __ldg(gnpad + pc + off) - __ldg(gnpad + pc - off);
-        Pv[0] += e0 * dn; Pv[1] += e1 * dn; Pv[2] += e2 * dn;
-        Qv[0] += e0 * dq; Qv[1] += e1 * dq; Qv[2] += e2 * dq;
-        TP += e0 * (__ldg(gLpad + pc + off) - __ldg(gLpad + pc - off)) +
-              e1 * (__ldg(gLpad + g.P + pc + off) - __ldg(gLpad + g.P + pc - off)) +
-              e2 * (__ldg(gLpad + 2 * g.P + pc + off) - __ldg(gLpad + 2 * g.P + pc - off));
-        TQ += e0 * (__ldg(Lpad + pc + off) - __ldg(Lpad + pc - off)) +
-              e1 * (__ldg(Lpad + g.P + pc + off) - __ldg(Lpad + g.P + pc - off)) +
-              e2 * (__ldg(Lpad + 2 * g.P + pc + off) - __ldg(Lpad + 2 * g.P + pc - off));
-    }
-    const T gv = gab[i];
-    const T nb = npad_b[pc];
-    const T na = npad_a[pc];
-    T lCa[3], Lv[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lCa[c] = lC_a[(long long)c * g.N + i];
-        Lv[c] = Lpad[(long long)c * g.P + pc];
-    }
-    const T own_n = (T)0.5 * coef * ((gv * Pv[0] + Qv[0]) * lCa[0] + (gv * Pv[1] + Qv[1]) * lCa[1] +
-                                     (gv * Pv[2] + Qv[2]) * lCa[2]);
-    const T own_g = Lv[0] * Pv[0] + Lv[1] * Pv[1] + Lv[2] * Pv[2];
-    (void)na;
-    ln[(long long)b * g.N + i] += -TP - gv * TQ;
-    ln[(long long)a * g.N + i] += own_n;
-    lg[i] += -nb * TQ + own_g;
-    (void)same;
+    lg[i] += lp;
+    if (own && na != (T)0) ln_a[i] += cl / na;
 }
 
 // ---------------------------------------------------------------------------
@@ -411,22 +411,23 @@ __global__ void k_adj_amp(Grid g, int M, const T *__restrict__ lF, const double 
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-#define LBE_ADJ_DISPATCH(p, CALL)                                                 \
+#define LBE_ADJ_DISPATCH(p, ...)                                                  \
     switch (p) {                                                                  \
-        case Prec::F64: { using S = double; using T = double; CALL; break; }     \
-        case Prec::F32: { using S = float; using T = float; CALL; break; }       \
+        case Prec::F64: { using S = double; using T = double; __VA_ARGS__; break; } \
+        case Prec::F32: { using S = float; using T = float; __VA_ARGS__; break; }   \
         default: return cudaErrorInvalidValue;                                    \
     }
 
 cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const uint32_t *mask, const void *C,
                                const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
-                               const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF,
+                               const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF, void *lmom,
                                cudaStream_t st) {
     const unsigned nb = (unsigned)((g.N + ANT - 1) / ANT);
+    const unsigned nbc = (unsigned)((g.N + ACT - 1) / ACT);
 #define LBE_ADJ_M(MM)                                                                                          \
-    k_adj_collide<S, T, MM><<<nb, ANT, 0, st>>>(g, (const S *)post, mask, (const T *)C, (const T *)F, ap,       \
+    k_adj_collide<S, T, MM><<<nbc, ACT, 0, st>>>(g, (const S *)post, mask, (const T *)C, (const T *)F, ap,       \
                                                 (const T *)lYf_in, (const T *)lYg_in, (const T *)lnd_in,       \
-                                                (T *)lYf_out, (T *)lYg_out, (T *)lC, (T *)lF)
+                                                (T *)lmom, (T *)lC, (T *)lF)
     LBE_ADJ_DISPATCH(p, {
         switch (ap.M) {
             case 1: LBE_ADJ_M(1); break;
@@ -435,32 +436,59 @@ cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const ui
             case 4: LBE_ADJ_M(4); break;
             default: return cudaErrorInvalidValue;
         }
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_adj_write<T><<<dim3(nb, (unsigned)ap.M), ANT, 0, st>>>(g, mask, ap, (const T *)lYf_in, (const T *)lYg_in,
+                                                                 (const T *)lnd_in, (const T *)lmom, (T *)lYf_out,
+                                                                 (T *)lYg_out);
     });
 #undef LBE_ADJ_M
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_shell(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st) {
+cudaError_t launch_adj_shell_prep(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.N + ANT - 1) / ANT);
-    if (fp64) {
+    if (fp64)
         k_adj_shell_prep<double><<<nb, ANT, 0, st>>>(g, (const double *)L.npad_a, (const double *)L.gab,
-                                                     (const double *)L.lC_a, L.coef, (double *)L.Lpad,
-                                                     (double *)L.gLpad);
-        k_adj_shell<double><<<nb, ANT, 0, st>>>(g, L.nhalf, L.hs, (const double *)L.unit, (const double *)L.npad_a,
-                                                (const double *)L.npad_b, (const double *)L.gnpad,
-                                                (const double *)L.gab, (const double *)L.lC_a,
-                                                (const double *)L.Lpad, (const double *)L.gLpad, L.coef, L.a == L.b,
-                                                (double *)L.ln, L.a, L.b, (double *)L.lg);
-    } else {
+                                                     (const double *)L.lC_a, (const double *)L.P,
+                                                     (const double *)L.C_a, L.coef, L.own, (double *)L.Lpad,
+                                                     (double *)L.gLpad, (double *)L.ln_a, (double *)L.lg);
+    else
         k_adj_shell_prep<float><<<nb, ANT, 0, st>>>(g, (const float *)L.npad_a, (const float *)L.gab,
-                                                    (const float *)L.lC_a, (float)L.coef, (float *)L.Lpad,
-                                                    (float *)L.gLpad);
-        k_adj_shell<float><<<nb, ANT, 0, st>>>(g, L.nhalf, L.hs, (const float *)L.unit, (const float *)L.npad_a,
-                                               (const float *)L.npad_b, (const float *)L.gnpad, (const float *)L.gab,
-                                               (const float *)L.lC_a, (const float *)L.Lpad, (const float *)L.gLpad,
-                                               (float)L.coef, L.a == L.b, (float *)L.ln, L.a, L.b, (float *)L.lg);
-    }
+                                                    (const float *)L.lC_a, (const float *)L.P, (const float *)L.C_a,
+                                                    (float)L.coef, L.own, (float *)L.Lpad, (float *)L.gLpad,
+                                                    (float *)L.ln_a, (float *)L.lg);
     return cudaGetLastError();
+}
+
+template <typename T, int S, int TZ, int TYB>
+cudaError_t launch_adj_tile(const AdjShellTile &L, cudaStream_t st);
+
+// Tile shapes equal those of the forward kernels, so the tensor-map boxes of shell_box() serve both.
+cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st) {
+    if (!fp64) {
+        switch (S) {
+            case 1: return launch_adj_tile<float, 1, 2, 16>(L, st);
+            case 2: return launch_adj_tile<float, 2, 2, 16>(L, st);
+            case 3: return launch_adj_tile<float, 3, 2, 16>(L, st);
+            case 4: return launch_adj_tile<float, 4, 2, 16>(L, st);
+            case 5: return launch_adj_tile<float, 5, 2, 16>(L, st);
+            case 6: return launch_adj_tile<float, 6, 2, 16>(L, st);
+            case 7: return launch_adj_tile<float, 7, 2, 16>(L, st);
+            case 8: return launch_adj_tile<float, 8, 1, 8>(L, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (S) {
+        case 1: return launch_adj_tile<double, 1, 1, 8>(L, st);
+        case 2: return launch_adj_tile<double, 2, 1, 8>(L, st);
+        case 3: return launch_adj_tile<double, 3, 1, 8>(L, st);
+        case 4: return launch_adj_tile<double, 4, 1, 8>(L, st);
+        case 5: return launch_adj_tile<double, 5, 1, 4>(L, st);
+        case 6: return launch_adj_tile<double, 6, 1, 4>(L, st);
+        case 7: return launch_adj_tile<double, 7, 1, 4>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_adj_contact(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,

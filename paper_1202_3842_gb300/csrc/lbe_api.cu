@@ -70,6 +70,8 @@ struct lbe_ctx {
     Buf err;
     Buf scratch64;  // FP64 scratch for getters: n [M][N] + J [M][3][N] (+ more)
     Buf partial, red_out;
+    Buf res_rec;             // densities recorded by lbe_get_residual [M][N] (FP64)
+    long long res_t0 = -1;   // step count of the record, -1: none
 
     // derived state
     bool geom_dirty = true, force_dirty = true, fields_dirty = true;
@@ -395,14 +397,17 @@ StepParams step_params(const lbe_ctx *c) {
     return sp;
 }
 
-// K1 -> K2 -> K3 for the current populations (fills npad, gab, gnpad, C).
-lbe_status force_stage(lbe_ctx *c) {
+// K1 -> K2 -> K3 for the populations pop (default: the current state); fills
+// npad, gab, gnpad, C.  With Pbase, the shell kernels also store P of every
+// pair into Pbase [npairs][3][N] (for the adjoint).
+lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = nullptr) {
     const bool f64 = prec_fp64(c->prec);
     const size_t rb = real_bytes(c);
+    if (!pop) pop = c->pop[c->cur].p;
     {
         StageTimer t(c, LBE_STAGE_DENSITY);
-            LAUNCH(launch_density(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->solid_links, c->M,
-                              c->n0, c->npad.p, (int *)c->err.p, c->stream),
+        LAUNCH(launch_density(c->prec, c->g, pop, (const uint32_t *)c->mask.p, c->solid_links, c->M, c->n0,
+                              c->npad.p, (int *)c->err.p, c->stream),
                "density kernel");
     }
     if (c->pairs.empty()) return LBE_OK;  // ideal gas: C stays zero
@@ -420,7 +425,8 @@ lbe_status force_stage(lbe_ctx *c) {
         LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
     }
     std::vector<int> first(c->M, 1);
-    for (auto &ps : c->pairs) {
+    for (size_t q = 0; q < c->pairs.size(); ++q) {
+        const PairShell &ps = c->pairs[q];
         ShellLaunch L{};
         L.grid = &c->g;
         L.map_n = &ps.map_n;
@@ -428,6 +434,7 @@ lbe_status force_stage(lbe_ctx *c) {
         L.npad_a = (const char *)c->npad.p + rb * ps.a * c->g.P;
         L.g_ab = (const char *)c->gab.p + rb * (ps.a * c->M + ps.b) * c->g.N;
         L.Cout = (char *)c->C.p + rb * 3 * ps.a * c->g.N;
+        L.Pout = Pbase ? (char *)Pbase + rb * 3 * q * c->g.N : nullptr;
         L.coef = ps.coef;
         L.accumulate = first[ps.a] ? 0 : 1;
         L.err = (int *)c->err.p;
@@ -612,7 +619,7 @@ void lbe_destroy(lbe_ctx *c) {
     c->ev_pool.clear();
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
-                  &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out};
+                  &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec};
     for (Buf *b : all) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     delete c;
@@ -678,6 +685,7 @@ lbe_status lbe_set_body_force(lbe_ctx *c, int s, const double gb[3]) {
 
 static void reset_counters(lbe_ctx *c) {
     c->steps = 0;
+    c->res_t0 = -1;
     c->flux_count = 0;
     cudaMemsetAsync(c->flux_acc.p, 0, 8 * MAXS, c->stream);
     cudaMemsetAsync(c->flux_last.p, 0, 8 * MAXS, c->stream);
@@ -930,6 +938,113 @@ lbe_status lbe_get_step_count(lbe_ctx *c, long long *steps) {
     return LBE_OK;
 }
 
+namespace {
+// Layout of a saved state: this header, then the populations as stored.
+struct StateHeader {
+    char magic[8];
+    int32_t version, nx, ny, nz, M, prec, flux_axis, flux_plane;
+    int64_t steps, flux_count;
+    double n0[MAXS], flux_acc[MAXS], flux_last[MAXS];
+    uint64_t pop_bytes;
+};
+const char kStateMagic[8] = {'L', 'B', 'E', 'S', 'T', 'A', 'T', 'E'};
+}  // namespace
+
+lbe_status lbe_save_state(lbe_ctx *c, void *host_buf, size_t *bytes) {
+    TRY(ready(c));
+    if (!bytes) return fail(c, LBE_ERR_INVALID_ARG, "null size pointer");
+    const size_t pop_bytes = (size_t)prec_bytes(c->prec) * c->M * 2 * Q * c->g.N;
+    const size_t total = sizeof(StateHeader) + pop_bytes;
+    if (!host_buf) {
+        *bytes = total;
+        return LBE_OK;
+    }
+    if (*bytes < total) return fail(c, LBE_ERR_INVALID_ARG, "state buffer of " + std::to_string(*bytes) +
+                                                             " bytes, the state needs " + std::to_string(total));
+    StateHeader h{};
+    std::memcpy(h.magic, kStateMagic, 8);
+    h.version = 1;
+    h.nx = c->g.nx;
+    h.ny = c->g.ny;
+    h.nz = c->g.nz;
+    h.M = c->M;
+    h.prec = (int32_t)c->prec;
+    h.flux_axis = c->flux_axis;
+    h.flux_plane = c->flux_plane;
+    h.steps = c->steps;
+    h.flux_count = c->flux_count;
+    for (int a = 0; a < MAXS; ++a) h.n0[a] = c->n0[a];
+    h.pop_bytes = pop_bytes;
+    CK(cudaMemcpyAsync(h.flux_acc, c->flux_acc.p, 8 * MAXS, cudaMemcpyDeviceToHost, c->stream), "copy flux");
+    CK(cudaMemcpyAsync(h.flux_last, c->flux_last.p, 8 * MAXS, cudaMemcpyDeviceToHost, c->stream), "copy flux");
+    CK(cudaMemcpyAsync((char *)host_buf + sizeof(StateHeader), c->pop[c->cur].p, pop_bytes, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "copy populations");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    std::memcpy(host_buf, &h, sizeof(h));
+    *bytes = total;
+    return LBE_OK;
+}
+
+lbe_status lbe_load_state(lbe_ctx *c, const void *host_buf, size_t bytes) {
+    TRY(ready(c));
+    if (!host_buf || bytes < sizeof(StateHeader)) return fail(c, LBE_ERR_INVALID_ARG, "no state in the buffer");
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof(h));
+    const size_t pop_bytes = (size_t)prec_bytes(c->prec) * c->M * 2 * Q * c->g.N;
+    if (std::memcmp(h.magic, kStateMagic, 8) != 0 || h.version != 1)
+        return fail(c, LBE_ERR_INVALID_ARG, "the buffer does not hold a saved state");
+    if (h.nx != c->g.nx || h.ny != c->g.ny || h.nz != c->g.nz || h.M != c->M || h.prec != (int32_t)c->prec ||
+        h.pop_bytes != pop_bytes || bytes < sizeof(StateHeader) + pop_bytes)
+        return fail(c, LBE_ERR_INVALID_ARG, "the saved state has another lattice size, species count or precision");
+    if (h.flux_plane >= 0) {
+        const int extent = h.flux_axis == 0 ? c->g.nx : (h.flux_axis == 1 ? c->g.ny : c->g.nz);
+        if (h.flux_axis < 0 || h.flux_axis > 2 || h.flux_plane >= extent)
+            return fail(c, LBE_ERR_INVALID_ARG, "the saved flux plane is out of range");
+    }
+    CK(cudaMemcpyAsync(c->pop[c->cur].p, (const char *)host_buf + sizeof(StateHeader), pop_bytes,
+                       cudaMemcpyHostToDevice, c->stream),
+       "copy populations");
+    CK(cudaMemcpyAsync(c->flux_acc.p, h.flux_acc, 8 * MAXS, cudaMemcpyHostToDevice, c->stream), "copy flux");
+    CK(cudaMemcpyAsync(c->flux_last.p, h.flux_last, 8 * MAXS, cudaMemcpyHostToDevice, c->stream), "copy flux");
+    CK(cudaStreamSynchronize(c->stream), "sync");
+    for (int a = 0; a < MAXS; ++a) c->n0[a] = h.n0[a];
+    c->steps = h.steps;
+    c->flux_count = h.flux_count;
+    c->flux_axis = h.flux_axis;
+    c->flux_plane = h.flux_plane;
+    c->res_t0 = -1;
+    if (c->flux_plane >= 0) TRY(dev_alloc(c, c->flux_buf, 8 * (size_t)c->M * plane_size(c)));
+    return LBE_OK;
+}
+
+lbe_status lbe_get_residual(lbe_ctx *c, double *res) {
+    TRY(ready(c));
+    if (!res) return fail(c, LBE_ERR_INVALID_ARG, "null output");
+    const long long N = c->g.N;
+    double *n, *J;
+    TRY(state_moments(c, &n, &J));
+    TRY(dev_alloc(c, c->res_rec, 8 * (size_t)c->M * N));
+    const bool have = c->res_t0 >= 0 && c->steps > c->res_t0;
+    InvN0 inv{};
+    for (int a = 0; a < c->M; ++a) {
+        const double n0 = c->n0[a] > 0.0 ? c->n0[a] : 1.0;
+        inv.v[a] = have ? 1.0 / ((double)(c->steps - c->res_t0) * n0) : 0.0;
+    }
+    double *out = J + (long long)c->M * 3 * N;  // free FP64 scratch of N values
+    LAUNCH(launch_residual(c->M, N, inv, n, (double *)c->res_rec.p, out, c->stream), "residual kernel");
+    double r[2] = {-1.0, -1.0};
+    if (have) {
+        LAUNCH(launch_reduce(out, N, (double *)c->partial.p, 1024, (double *)c->red_out.p, c->stream),
+               "reduce residual");
+        CK(cudaMemcpyAsync(r, c->red_out.p, 16, cudaMemcpyDeviceToHost, c->stream), "copy");
+    }
+    TRY(check_error_word(c));
+    *res = have ? r[1] : -1.0;
+    c->res_t0 = c->steps;
+    return LBE_OK;
+}
+
 lbe_status lbe_get_link_mask(lbe_ctx *c, uint32_t *out) {
     TRY(ready(c));
     if (!out) return fail(c, LBE_ERR_INVALID_ARG, "null output");
@@ -979,13 +1094,21 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     const long long steps_before = c->steps;
     const int old_axis = c->flux_axis, old_plane = c->flux_plane;
 
-    std::vector<Buf> ck(nseg), seg(kseg);
-    Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, hs, unit, outA, red;
+    // Device memory: checkpoints ck[s] (state at step s*K), the states 1..K-1 of the segment being
+    // reversed (seg[k]), and per segment step the fields of its force stage (slot[k]): npad [M][P],
+    // gnpad [M][M][P], gab [M][M][N], C [M][3][N], P [npairs][3][N].
+    const int npairs = (int)c->pairs.size();
+    const size_t sl_npad = 0, sl_gnpad = sl_npad + rb * M * P, sl_gab = sl_gnpad + rb * M * M * P,
+                 sl_C = sl_gab + rb * M * M * N, sl_P = sl_C + rb * M * 3 * N,
+                 slot_bytes = sl_P + rb * 3 * (size_t)std::max(npairs, 1) * N;
+    std::vector<Buf> ck(nseg), seg(kseg), slot(kseg);
+    Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, lmom, outA, red;
     auto release = [&]() {
         for (auto &b : ck) dev_free(c, b);
         for (auto &b : seg) dev_free(c, b);
+        for (auto &b : slot) dev_free(c, b);
         Buf *all[] = {&lYf[0], &lYf[1], &lYg[0], &lYg[1], &lnd[0], &lnd[1], &lC, &lF, &lg, &Lpad, &gLpad,
-                      &lnbar, &hs, &unit, &outA, &red};
+                      &lnbar, &lmom, &outA, &red};
         for (Buf *b : all) dev_free(c, *b);
     };
     auto alloc = [&](Buf &b, size_t bytes, bool zero) -> lbe_status {
@@ -1004,7 +1127,8 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
         }                         \
     } while (0)
     for (auto &b : ck) ATRY(alloc(b, pop_bytes, false));
-    for (auto &b : seg) ATRY(alloc(b, pop_bytes, false));
+    for (int k = 1; k < kseg; ++k) ATRY(alloc(seg[k], pop_bytes, false));
+    for (auto &b : slot) ATRY(alloc(b, slot_bytes, false));
     for (int k = 0; k < 2; ++k) {
         ATRY(alloc(lYf[k], rb * M * Q * N, true));
         ATRY(alloc(lYg[k], rb * M * Q * N, true));
@@ -1016,42 +1140,18 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     ATRY(alloc(Lpad, rb * 3 * P, true));
     ATRY(alloc(gLpad, rb * 3 * P, true));
     ATRY(alloc(lnbar, rb * M * P, true));
+    ATRY(alloc(lmom, rb * M * 5 * N, false));
     ATRY(alloc(outA, 8 * N, false));
     ATRY(alloc(red, 8 * N, false));
 
-    // half-shell tables of every pair: padded offset, (ex, ey, ez), unit vectors
-    std::vector<int4> hs_h;
-    std::vector<double> unit_d;
-    std::vector<int> hs_start;
-    for (auto &ps : c->pairs) {
-        hs_start.push_back((int)hs_h.size());
-        const int S = ps.S;
-        for (int z = -S; z <= S; ++z)
-            for (int y = -S; y <= S; ++y)
-                for (int x = -S; x <= S; ++x)
-                    if (in_shell(S, x, y, z) && positive_half(x, y, z)) {
-                        const int off = x + c->g.px * (y + c->g.py * z);
-                        hs_h.push_back(make_int4(off, x, y, z));
-                        const double L = std::sqrt((double)(x * x + y * y + z * z));
-                        unit_d.push_back(x / L);
-                        unit_d.push_back(y / L);
-                        unit_d.push_back(z / L);
-                    }
-    }
-    hs_start.push_back((int)hs_h.size());
-    if (!hs_h.empty()) {
-        ATRY(alloc(hs, sizeof(int4) * hs_h.size(), false));
-        ATRY(alloc(unit, rb * unit_d.size(), false));
-        CK(cudaMemcpyAsync(hs.p, hs_h.data(), sizeof(int4) * hs_h.size(), cudaMemcpyHostToDevice, c->stream),
-           "copy half shells");
-        if (f64) {
-            CK(cudaMemcpyAsync(unit.p, unit_d.data(), 8 * unit_d.size(), cudaMemcpyHostToDevice, c->stream),
-               "copy unit vectors");
-        } else {
-            std::vector<float> uf(unit_d.begin(), unit_d.end());
-            CK(cudaMemcpyAsync(unit.p, uf.data(), 4 * uf.size(), cudaMemcpyHostToDevice, c->stream),
-               "copy unit vectors");
-            CK(cudaStreamSynchronize(c->stream), "sync");
+    // tensor maps of the padded Lambda_c and (g Lambda)_c with the box of each pair's shell
+    std::vector<CUtensorMap> mapL(3 * npairs), mapgL(3 * npairs);
+    for (int q = 0; q < npairs; ++q) {
+        int bx = 0, by = 0;
+        shell_box(f64, c->pairs[q].S, &bx, &by);
+        for (int cc = 0; cc < 3; ++cc) {
+            ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + rb * cc * P, bx, by));
+            ATRY(make_map(c, &mapgL[3 * q + cc], (char *)gLpad.p + rb * cc * P, bx, by));
         }
     }
 
@@ -1088,45 +1188,67 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     int cl = 0;
     for (int s = nseg - 1; s >= 0; --s) {
         const int nst = std::min(K, T - s * K);
-        CK(cudaMemcpyAsync(c->pop[c->cur].p, ck[s].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "restore");
+        auto state = [&](int k) -> void * { return k == 0 ? ck[s].p : seg[k].p; };
+        // recompute the segment: the force stage of every state (kept in its slot) and the states
         for (int k = 0; k < nst; ++k) {
-            CK(cudaMemcpyAsync(seg[k].p, c->pop[c->cur].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream), "save");
-            ATRY(step_once(c, sp0, 0));
+            char *sl = (char *)slot[k].p;
+            ATRY(force_stage(c, state(k), npairs ? sl + sl_P : nullptr));
+            CK(cudaMemcpyAsync(sl + sl_npad, c->npad.p, rb * M * P, cudaMemcpyDeviceToDevice, c->stream), "keep npad");
+            if (npairs) {
+                CK(cudaMemcpyAsync(sl + sl_gnpad, c->gnpad.p, rb * M * M * P, cudaMemcpyDeviceToDevice, c->stream),
+                   "keep gnpad");
+                CK(cudaMemcpyAsync(sl + sl_gab, c->gab.p, rb * M * M * N, cudaMemcpyDeviceToDevice, c->stream),
+                   "keep gab");
+            }
+            CK(cudaMemcpyAsync(sl + sl_C, c->C.p, rb * M * 3 * N, cudaMemcpyDeviceToDevice, c->stream), "keep C");
+            if (k + 1 < nst) {
+                StageTimer tm(c, LBE_STAGE_COLLIDE);
+                LAUNCH(launch_collide(c->prec, c->g, state(k), state(k + 1), (const uint32_t *)c->mask.p,
+                                      c->solid_links, c->C.p, c->F.p, sp0, (double *)c->flux_buf.p, c->stream),
+                       "collide kernel");
+            }
         }
         for (int k = nst - 1; k >= 0; --k) {
-            CK(cudaMemcpyAsync(c->pop[c->cur].p, seg[k].p, pop_bytes, cudaMemcpyDeviceToDevice, c->stream),
-               "restore step");
-            ATRY(force_stage(c));
-            LAUNCH(launch_adj_collide(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p,
-                                      ap, lYf[cl].p, lYg[cl].p, lnd[cl].p, lYf[1 - cl].p, lYg[1 - cl].p, lC.p,
-                                      lF.p, c->stream),
+            const char *sl = (const char *)slot[k].p;
+            LAUNCH(launch_adj_collide(c->prec, c->g, state(k), (const uint32_t *)c->mask.p, sl + sl_C, c->F.p, ap,
+                                      lYf[cl].p, lYg[cl].p, lnd[cl].p, lYf[1 - cl].p, lYg[1 - cl].p, lC.p, lF.p,
+                                      lmom.p, c->stream),
                    "adjoint collide");
+            c->launches += 1;  // k_adj_collide + k_adj_write
             CK(cudaMemsetAsync(lnd[1 - cl].p, 0, rb * M * N, c->stream), "memset");
             CK(cudaMemsetAsync(lg.p, 0, rb * M * M * N, c->stream), "memset");
-            for (size_t q = 0; q < c->pairs.size(); ++q) {
+            std::vector<int> own(M, 1);
+            for (int q = 0; q < npairs; ++q) {
                 const auto &ps = c->pairs[q];
                 AdjShell L{};
-                L.hs = (const int4 *)hs.p + hs_start[q];
-                L.unit = (const char *)unit.p + rb * 3 * hs_start[q];
-                L.nhalf = hs_start[q + 1] - hs_start[q];
-                L.npad_a = (const char *)c->npad.p + rb * ps.a * P;
-                L.npad_b = (const char *)c->npad.p + rb * ps.b * P;
-                L.gnpad = (const char *)c->gnpad.p + rb * (ps.a * M + ps.b) * P;
-                L.gab = (const char *)c->gab.p + rb * (ps.a * M + ps.b) * N;
+                L.npad_a = sl + sl_npad + rb * ps.a * P;
+                L.gab = sl + sl_gab + rb * (ps.a * M + ps.b) * N;
                 L.lC_a = (const char *)lC.p + rb * 3 * ps.a * N;
+                L.P = sl + sl_P + rb * 3 * q * N;
+                L.C_a = sl + sl_C + rb * 3 * ps.a * N;
                 L.Lpad = Lpad.p;
                 L.gLpad = gLpad.p;
                 L.coef = ps.coef;
-                L.ln = lnd[1 - cl].p;
+                L.own = own[ps.a];
+                own[ps.a] = 0;
+                L.ln_a = (char *)lnd[1 - cl].p + rb * ps.a * N;
                 L.lg = (char *)lg.p + rb * (ps.a * M + ps.b) * N;
-                L.a = ps.a;
-                L.b = ps.b;
-                LAUNCH(launch_adj_shell(f64, c->g, L, c->stream), "adjoint shell");
-                c->launches += 1;
+                LAUNCH(launch_adj_shell_prep(f64, c->g, L, c->stream), "adjoint shell prep");
+                AdjShellTile LT{};
+                LT.grid = &c->g;
+                LT.maps_L = &mapL[3 * q];
+                LT.maps_gL = &mapgL[3 * q];
+                LT.npad_b = sl + sl_npad + rb * ps.b * P;
+                LT.g_ab = L.gab;
+                LT.ln_b = (char *)lnd[1 - cl].p + rb * ps.b * N;
+                LT.lg_ab = L.lg;
+                LT.err = (int *)c->err.p;
+                LAUNCH(launch_adj_shell_tile(f64, ps.S, LT, c->stream), "adjoint shell");
+                c->launches += 2;  // one launch per component
             }
-            if (!c->pairs.empty()) {
-                LAUNCH(launch_adj_contact(f64, c->g, c->cparams, c->brows, (const uint32_t *)c->mask.p, c->npad.p,
-                                          lg.p, lnbar.p, lnd[1 - cl].p, c->stream),
+            if (npairs) {
+                LAUNCH(launch_adj_contact(f64, c->g, c->cparams, c->brows, (const uint32_t *)c->mask.p,
+                                          sl + sl_npad, lg.p, lnbar.p, lnd[1 - cl].p, c->stream),
                        "adjoint contact");
                 c->launches += 1;
             }

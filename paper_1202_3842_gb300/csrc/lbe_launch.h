@@ -66,6 +66,7 @@ struct ShellLaunch {
     const void *npad_a;
     const void *g_ab;
     void *Cout;
+    void *Pout;  // NULL, or [3][N]: P = sum_e e^ n_b(r+e) of the pair (for the adjoint)
     double coef;
     int accumulate;
     int *err;
@@ -110,6 +111,12 @@ cudaError_t launch_reduce(const double *x, long long n, double *partial, int npa
 // u [3][N] = J/n summed over species s (all for s < 0); speed [N] = |u| (either may be NULL).
 cudaError_t launch_velocity(int M, long long N, int s, const double *n, const double *J, double *u, double *speed,
                             cudaStream_t st);
+// Steady-state residual: out[i] = max_a |n_a(i) - rec_a(i)| * inv.v[a]; rec <- n.
+struct InvN0 {
+    double v[MAXS];
+};
+cudaError_t launch_residual(int M, long long N, const InvN0 &inv, const double *n, double *rec, double *out,
+                            cudaStream_t st);
 // Convert a compute-precision field to FP64.
 cudaError_t launch_to_f64(bool fp64, const void *src, long long n, double *dst, cudaStream_t st);
 // Copy the interior of a padded field to a dense FP64 array.
@@ -127,23 +134,38 @@ struct AdjParams {
     SpeciesConst sp[MAXS];
 };
 
+// Node-local part of the shell transpose of pair (a, b) (k_adj_shell_prep).
 struct AdjShell {
-    const int4 *hs;    // half shell: padded offset, ex, ey, ez
-    const void *unit;  // unit vectors [nhalf][3] (compute precision)
-    int nhalf;
-    const void *npad_a, *npad_b, *gnpad, *gab, *lC_a;
-    void *Lpad, *gLpad;  // [3][P] work fields
+    const void *npad_a;  // padded n_a
+    const void *gab;     // g_ab [N]
+    const void *lC_a;    // adjoint of C^a [3][N]
+    const void *P;       // P = sum_e e^ n_b(r+e) of the pair [3][N] (forward recomputation)
+    const void *C_a;     // C^a [3][N] of the forward state
+    void *Lpad, *gLpad;  // out: padded Lambda and g*Lambda [3][P]
     double coef;
-    void *ln;  // [M][N] density adjoint (accumulated)
-    void *lg;  // [N] contact-value adjoint of this pair (accumulated)
-    int a, b;
+    int own;    // add the own-node density term of species a (once per species)
+    void *ln_a; // [N] density adjoint of species a (accumulated)
+    void *lg;   // [N] contact-value adjoint of this pair (accumulated)
+};
+
+// Shell sums of the transpose of pair (a, b): three launches, one per component.
+struct AdjShellTile {
+    const Grid *grid;
+    const CUtensorMap *maps_L;   // [3] padded Lambda_c, box of shell_box(S)
+    const CUtensorMap *maps_gL;  // [3] padded (g Lambda)_c
+    const void *npad_b;
+    const void *g_ab;
+    void *ln_b;   // [N] density adjoint of species b (accumulated)
+    void *lg_ab;  // [N] contact-value adjoint of the pair (accumulated)
+    int *err;
 };
 
 cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const uint32_t *mask, const void *C,
                                const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
                                const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF,
-                               cudaStream_t st);
-cudaError_t launch_adj_shell(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st);
+                               void *lmom /* [M][5][N] scratch */, cudaStream_t st);
+cudaError_t launch_adj_shell_prep(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st);
+cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st);
 cudaError_t launch_adj_contact(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
                                const uint32_t *mask, const void *npad, const void *lg, void *lnbar, void *ln,
                                cudaStream_t st);

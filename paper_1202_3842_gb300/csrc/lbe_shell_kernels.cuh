@@ -15,7 +15,9 @@
 // plane, completion on an mbarrier per ring slot).  The plain kernel gives
 // each thread one output per plane; the z-blocked kernel gives each thread TZ
 // outputs along z and reuses every shared-memory read across them.  The shell
-// offsets and unit vectors are compile-time immediates.
+// offsets and unit vectors are compile-time immediates.  When Pout is given,
+// the kernels also store P = sum_e e^ n_b(r+e) of the pair ([3][N]), which the
+// discrete adjoint needs.
 #pragma once
 #include <utility>
 
@@ -74,7 +76,7 @@ template <typename T, int S>
 __global__ void __launch_bounds__(32 * ShellTile<T, S>::TY)
     k_shell_force(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn,
                   Grid g, int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab,
-                  T *__restrict__ Cout, T coef, int accumulate, int *err) {
+                  T *__restrict__ Cout, T *__restrict__ Pout, T coef, int accumulate, int *err) {
     using Tl = ShellTile<T, S>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(32 * ShellTile<T, S>::TY)
                     *o += v;
                 else
                     *o = v;
+                if (Pout) Pout[(long long)c * g.N + i] = an[c];
             }
         }
         __syncthreads();
@@ -240,8 +243,8 @@ __device__ __forceinline__ void all_columns(const T *const *sb, T (*an)[3], T (*
 template <typename T, int S, int TZ, int TYB>
 __global__ void __launch_bounds__(32 * TYB, 1)
     k_shell_force_zb(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn, Grid g,
-                     int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab, T *__restrict__ Cout, T coef,
-                     int accumulate, int *err) {
+                     int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab, T *__restrict__ Cout,
+                     T *__restrict__ Pout, T coef, int accumulate, int *err) {
     using Tl = ShellTileZ<T, S, TZ, TYB>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
@@ -327,6 +330,10 @@ __global__ void __launch_bounds__(32 * TYB, 1)
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         Cout[(long long)c * g.N + idx[t]] = old[t][c] + pre * (half * gr[t] * an[t][c] + half * ag[t][c]);
+                    if (Pout) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Pout[(long long)c * g.N + idx[t]] = an[t][c];
+                    }
                 }
             }
         }
@@ -353,8 +360,8 @@ cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
     dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
     const int ox = ((g.H - S) % Tl::A + Tl::A) % Tl::A;
     k_shell_force_zb<T, S, TZ, TYB><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
-                                                              (const T *)L.g_ab, (T *)L.Cout, (T)L.coef,
-                                                              L.accumulate, L.err);
+                                                              (const T *)L.g_ab, (T *)L.Cout, (T *)L.Pout,
+                                                              (T)L.coef, L.accumulate, L.err);
     return cudaGetLastError();
 }
 
@@ -374,8 +381,8 @@ cudaError_t launch_one(const ShellLaunch &L, cudaStream_t st) {
     const int A = Tl::A;
     const int ox = ((g.H - S) % A + A) % A;
     k_shell_force<T, S><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
-                                                       (const T *)L.g_ab, (T *)L.Cout, (T)L.coef, L.accumulate,
-                                                       L.err);
+                                                       (const T *)L.g_ab, (T *)L.Cout, (T *)L.Pout, (T)L.coef,
+                                                       L.accumulate, L.err);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,9 @@ def lib():
             "lbe_get_stage_times": [_P, _D, ctypes.POINTER(ctypes.c_longlong)],
             "lbe_get_mass_noalloc": [_P, _D],
             "lbe_adjoint_flux_gradient": [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D],
+            "lbe_save_state": [_P, _P, ctypes.POINTER(ctypes.c_size_t)],
+            "lbe_load_state": [_P, _P, ctypes.c_size_t],
+            "lbe_get_residual": [_P, _D],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -292,6 +295,26 @@ def lbe_get_step_count(ctx):
     return v.value
 
 
+def lbe_save_state(ctx):
+    """The state as bytes (populations as stored, n0, step count, flux plane and accumulators)."""
+    n = ctypes.c_size_t(0)
+    _check(lib().lbe_save_state(ctx, None, ctypes.byref(n)), ctx)
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().lbe_save_state(ctx, ctypes.cast(buf, _P), ctypes.byref(n)), ctx)
+    return buf.raw[:n.value]
+
+
+def lbe_load_state(ctx, state):
+    buf = ctypes.create_string_buffer(bytes(state), len(state))
+    _check(lib().lbe_load_state(ctx, ctypes.cast(buf, _P), len(state)), ctx)
+
+
+def lbe_get_residual(ctx):
+    v = ctypes.c_double(0.0)
+    _check(lib().lbe_get_residual(ctx, ctypes.byref(v)), ctx)
+    return v.value
+
+
 def lbe_get_link_mask(ctx, N):
     out = np.empty(N, dtype=np.uint32)
     _check(lib().lbe_get_link_mask(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), ctx)
@@ -442,6 +465,16 @@ class Simulation:
 
     def link_mask(self):
         return lbe_get_link_mask(self._h, self.N)
+
+    def save_state(self):
+        return lbe_save_state(self._h)
+
+    def load_state(self, state):
+        lbe_load_state(self._h, state)
+
+    def residual(self):
+        """max |n(t) - n(t0)| / ((t - t0) n0) since the previous call (-1 on the first call)."""
+        return lbe_get_residual(self._h)
 
     def launch_count(self):
         return lbe_get_launch_count(self._h)
