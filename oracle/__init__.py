@@ -55,6 +55,7 @@ def lib():
         L.or_set_wall_potential.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_dbl_p]
         L.or_set_body_force.argtypes = [ctypes.c_void_p, ctypes.c_int, _c_dbl_p]
         L.or_set_consistent_moments.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_set_scheme.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.or_set_flux_plane.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
         L.or_init_density.argtypes = [ctypes.c_void_p, ctypes.c_int, _c_dbl_p]
         L.or_set_populations.argtypes = [ctypes.c_void_p, ctypes.c_int, _c_dbl_p, _c_dbl_p]
@@ -64,10 +65,6 @@ def lib():
         L.or_get_flux.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_long_p]
         L.or_steps_done.argtypes = [ctypes.c_void_p]
         L.or_steps_done.restype = ctypes.c_long
-        if hasattr(L, "or_adjoint_flux_gradient"):
-            L.or_adjoint_flux_gradient.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                   ctypes.c_int, _c_dbl_p, _c_dbl_p, _c_dbl_p]
-            L.or_adjoint_flux_gradient.restype = ctypes.c_int
         _LIB = L
     return _LIB
 
@@ -223,6 +220,12 @@ class Sim:
     def set_consistent_moments(self, on):
         lib().or_set_consistent_moments(self._h, int(bool(on)))
 
+    def set_scheme(self, scheme):
+        """0 DD-TR (default), 1 SD-TR, 2 SD-EU, 3 DD-EU (Sec. "Results": single or double distribution,
+        Euler or trapezoidal integration)."""
+        if lib().or_set_scheme(self._h, int(scheme)) != 0:
+            raise ValueError("unknown scheme %r" % (scheme,))
+
     def set_flux_plane(self, axis, plane):
         lib().or_set_flux_plane(self._h, int(axis), int(plane))
 
@@ -261,16 +264,3 @@ class Sim:
 
     def steps_done(self):
         return lib().or_steps_done(self._h)
-
-    def adjoint_flux_gradient(self, nsteps, ckpt_every, axis, plane):
-        """Gradient of the time-averaged flux over the next nsteps w.r.t. the wall amplitude a(r) and
-        the body force of every species (summed).  Returns (Phi_bar, dPhi/da [N], dPhi/dg [3])."""
-        da = np.zeros(self.N)
-        dg = np.zeros(3)
-        phi = np.zeros(1)
-        rc = lib().or_adjoint_flux_gradient(self._h, int(nsteps), int(ckpt_every), int(axis), int(plane),
-                                            _p(da, ctypes.c_double), _p(dg, ctypes.c_double),
-                                            _p(phi, ctypes.c_double))
-        if rc != 0:
-            raise RuntimeError("oracle adjoint failed: %d" % rc)
-        return phi[0], da, dg

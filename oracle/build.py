@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["lbe_oracle.c", "lbe_oracle_adjoint.c"]
+SOURCES = ["lbe_oracle.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbe_oracle.so")
 

@@ -36,6 +36,16 @@
  *              on strongly compressed starts because the dropped d Pi/d n
  *              term of S_g is then not small).
  *   S_g      : the coefficient of H2 in the C^mf term is 4, as printed.
+ *   schemes  : (Sec. "Results") DD-TR is the default; the ablations are
+ *              SD-TR: one distribution f, S = S_f with the whole force, and the
+ *                     TR moments J = J~ + (h/2)(C^mf + nF) from f~;
+ *              SD-EU: one distribution, Euler update
+ *                     f* = f + (1/tau)(f_eq - f) + h S_f with J = sum c f;
+ *              DD-EU: both distributions with the Euler update and
+ *                     J = sum c g, Pi = sum g.
+ *              Euler and trapezoidal updates relax at the same rate 1/tau
+ *              (omega_EU h = 1/tau).  In the SD schemes g is not evolved: it
+ *              is kept equal to f.
  *   force    : F = -grad_h V + g with the isotropic D3Q19 gradient.
  *   init     : f~ = g~ = w_p n(r,0) on fluid nodes, zero on solid nodes.
  *   C^visc   : not in this oracle (disabled in the hot path).
@@ -333,6 +343,7 @@ typedef struct {
     double sigma[MAXS], tau[MAXS];
     double gbody[MAXS][3];
     int consistent_moments;
+    int scheme;          /* 0 DD-TR, 1 SD-TR, 2 SD-EU, 3 DD-EU */
     uint8_t *solid;      /* [N] */
     double *V;           /* [M][N] external potential per species */
     double *phi, *amp;   /* [N] wall potential shape and amplitude (a*phi added to every species) */
@@ -417,6 +428,17 @@ int or_set_consistent_moments(or_sim *s, int on) {
     return 0;
 }
 
+enum { DD_TR = 0, SD_TR = 1, SD_EU = 2, DD_EU = 3 };
+
+int or_set_scheme(or_sim *s, int scheme) {
+    if (scheme < DD_TR || scheme > DD_EU) return -1;
+    s->scheme = scheme;
+    return 0;
+}
+
+static int single_distribution(const or_sim *s) { return s->scheme == SD_TR || s->scheme == SD_EU; }
+static int trapezoidal(const or_sim *s) { return s->scheme == DD_TR || s->scheme == SD_TR; }
+
 int or_set_flux_plane(or_sim *s, int axis, int plane) {
     if (axis < 0 || axis > 2) return -1;
     s->flux_axis = axis;
@@ -466,8 +488,9 @@ static void compute_forces(or_sim *s) {
 
 /* Moments of the streamed populations and the physical moments (Sec. "Hard
  * sphere fluid mixture", moment equations): n = sum f~, Pi~ = sum g~,
- * J~ = sum c g~, then J and Pi by the reading stated in the header.  Fills
- * s->n, s->gpair, s->Cmf, s->F, s->J, s->Pi. */
+ * J~ = sum c g~, then J and Pi by the reading stated in the header.  The SD
+ * schemes take J~ from f~ and have no Pi (set to n); the EU schemes use the
+ * plain moments.  Fills s->n, s->gpair, s->Cmf, s->F, s->J, s->Pi. */
 static void compute_moments(or_sim *s) {
     long N = s->N;
     int M = s->M;
@@ -484,9 +507,10 @@ static void compute_moments(or_sim *s) {
     for (int a = 0; a < M; ++a)
         for (long i = 0; i < N; ++i) {
             double Pit = 0.0, Jt[3] = {0.0, 0.0, 0.0};
+            const double *mom = single_distribution(s) ? s->f : s->gd;
             if (!s->solid[i])
                 for (int p = 0; p < Q; ++p) {
-                    double gv = s->gd[((long)a * Q + p) * N + i];
+                    double gv = mom[((long)a * Q + p) * N + i];
                     Pit += gv;
                     for (int c = 0; c < 3; ++c) Jt[c] += CV[p][c] * gv;
                 }
@@ -497,12 +521,24 @@ static void compute_moments(or_sim *s) {
                 nF[c] = nn * s->F[((long)a * 3 + c) * N + i];
             }
             double J[3];
-            for (int c = 0; c < 3; ++c)
-                J[c] = s->consistent_moments ? Jt[c] + 0.5 * nF[c] : Jt[c] + 0.5 * (Cm[c] + nF[c]);
+            for (int c = 0; c < 3; ++c) {
+                if (s->scheme == DD_TR)
+                    J[c] = s->consistent_moments ? Jt[c] + 0.5 * nF[c] : Jt[c] + 0.5 * (Cm[c] + nF[c]);
+                else if (s->scheme == SD_TR)
+                    J[c] = Jt[c] + 0.5 * (Cm[c] + nF[c]);
+                else
+                    J[c] = Jt[c];
+            }
             double ua[3];
             for (int c = 0; c < 3; ++c) ua[c] = (nn > 0.0) ? J[c] / nn : 0.0;
             double Cu = Cm[0] * ua[0] + Cm[1] * ua[1] + Cm[2] * ua[2];
-            double Pi = s->consistent_moments ? Pit + 0.5 * BETA * Cu : Pit - 0.5 * Cu;
+            double Pi;
+            if (s->scheme == DD_TR)
+                Pi = s->consistent_moments ? Pit + 0.5 * BETA * Cu : Pit - 0.5 * Cu;
+            else if (s->scheme == DD_EU)
+                Pi = Pit;
+            else
+                Pi = nn;
             if (s->solid[i]) {
                 for (int c = 0; c < 3; ++c) J[c] = 0.0;
                 Pi = 0.0;
@@ -516,7 +552,9 @@ static void compute_moments(or_sim *s) {
  * update): collide f~ and g~ with the explicit TR kernel
  *   f~* = f~ + h [omega (f_eq - f~) + S_f] / (1 + omega h / 2)
  * (derived from f~ = f - h Omega/2 and f~(r + c h, t + h) = f~ + h Omega),
- * then stream with mid-point bounce-back. */
+ * then stream with mid-point bounce-back.  The EU schemes collide with
+ *   f* = f + (1/tau)(f_eq - f) + h S_f  (Sec. "Ideal fluid", Euler update);
+ * the SD schemes collide f only and copy it to g. */
 static void one_step(or_sim *s) {
     long N = s->N;
     int M = s->M;
@@ -564,7 +602,8 @@ static void one_step(or_sim *s) {
                 Cm[c] = s->Cmf[((long)a * 3 + c) * N + i];
                 nF[c] = nn * s->F[((long)a * 3 + c) * N + i];
             }
-            double omega = 1.0 / (s->tau[a] - 0.5); /* omega h, h = 1 */
+            double omega = 1.0 / (s->tau[a] - 0.5); /* omega h, h = 1 (TR) */
+            double omega_eu = 1.0 / s->tau[a];       /* omega h of the Euler update */
             for (int p = 0; p < Q; ++p) {
                 double H1[3], H2[3][3];
                 hermite(p, H1, H2);
@@ -593,8 +632,14 @@ static void one_step(or_sim *s) {
                 Sg *= wp;
                 long k = ((long)a * Q + p) * N + i;
                 double ft = s->f[k], gt = s->gd[k];
-                s->fpost[k] = ft + (omega * (feq - ft) + Sf) / (1.0 + 0.5 * omega);
-                s->gpost[k] = gt + (omega * (geq - gt) + Sg) / (1.0 + 0.5 * omega);
+                if (trapezoidal(s)) {
+                    s->fpost[k] = ft + (omega * (feq - ft) + Sf) / (1.0 + 0.5 * omega);
+                    s->gpost[k] = gt + (omega * (geq - gt) + Sg) / (1.0 + 0.5 * omega);
+                } else {
+                    s->fpost[k] = ft + omega_eu * (feq - ft) + Sf;
+                    s->gpost[k] = gt + omega_eu * (geq - gt) + Sg;
+                }
+                if (single_distribution(s)) s->gpost[k] = s->fpost[k];
             }
         }
     }
