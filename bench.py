@@ -322,6 +322,27 @@ def make_sim(w, arrays, prec):
     return sim
 
 
+def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof):
+    """Each stage kernel against its own bound, from the live per-stage event times.  Algorithmic bytes
+    per launch: K1 reads 19 f~ and writes one padded density per node and species; K4 reads and writes
+    f~ and g~ (76 populations) per node and species; K2 reads the padded densities and writes g and g n
+    of every ordered pair.  K3 is the roofline of the dominant-kernel entry when it dominates."""
+    rb = 8 if prec == "fp64" else 4
+    alg = {"density": N * M * (QPOP * sb + rb),
+           "collide": N * M * 4 * QPOP * sb,
+           "contact": N * (M * rb + 2 * M * M * rb)}
+    out = {}
+    for k, b in alg.items():
+        if k not in stages or stages[k][1] == 0:
+            continue
+        t = stages[k][0] / stages[k][1] * 1e-3
+        out[k] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
+                  "achieved_gbs": b / t / 1e9, "frac_of_measured_hbm": b / t / 1e9 / hbm}
+    if "shell" in stages and roof.get("bound") == "alu":
+        out["shell"] = {"bound": "alu", "achieved_tflops": roof["achieved"], "frac": roof["frac"]}
+    return out
+
+
 def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_kind, sampler=None):
     """Time `steps` DD-TR steps of workload wname after `warmup` untimed ones; per-stage device times from
     CUDA events on the launching stream; returns the result fields and the input arrays."""
@@ -401,7 +422,10 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
                 "launches": dom_n, "avg_launch_ms": per_launch_ms,
                 "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % clk}
     step_bytes = N * M * 4 * QPOP * sb
+    hbm = float(peaks["hbm_gbs"])
+    res_kernels = kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof)
     res = {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
+           "mlups_nodes": value / M,
            "config": {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "nodes": N,
                       "species": M,
                       "l2": "inputs larger than L2: population buffers %.2f GB each" % (N * M * 2 * QPOP * sb / 1e9),
@@ -409,6 +433,8 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
            "roofline": roof,
            "stage_ms_per_step": {k: v[0] / steps for k, v in stages.items()},
            "population_gbs_whole_step": step_bytes / (ms_step * 1e-3) / 1e9,
+           "population_gbs_whole_step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+           "kernels": res_kernels,
            "gpu_launches": launches, "state_after": state,
            "max_u_over_vT_after": umax / math.sqrt(1.0 / 3.0)}
     if clocks is not None:
@@ -483,8 +509,8 @@ def run_ours(args):
               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": core["ms_per_step"],
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
               "data": "synthetic (seeded inputs of the workload's shape and distribution)"}
-    for k in ("config", "roofline", "stage_ms_per_step", "population_gbs_whole_step", "gpu_launches", "clocks",
-              "state_after", "max_u_over_vT_after"):
+    for k in ("config", "roofline", "mlups_nodes", "kernels", "stage_ms_per_step", "population_gbs_whole_step",
+              "population_gbs_whole_step_frac", "gpu_launches", "clocks", "state_after", "max_u_over_vT_after"):
         result[k] = core.get(k)
 
     # end to end through the C ABI with host buffers: the timed region holds the host->device copy of the

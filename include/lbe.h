@@ -62,8 +62,15 @@ typedef enum {
     LBE_FP16_SHIFTED = 3
 } lbe_precision;
 
-/* Collision scheme (Sec. "Results": single/double distribution, Euler or
- * trapezoidal).  Only LBE_DD_TR is implemented. */
+/* Collision scheme (Sec. "Results": single (SD) or double (DD) distribution,
+ * Euler (EU) or trapezoidal (TR) integration).  LBE_DD_TR is the method; the
+ * others are ablations for accuracy studies (FP64 or FP32 storage, one or two
+ * species; LBE_ERR_UNSUPPORTED otherwise):
+ *   LBE_SD_TR: f only, S_f with the whole force, J = J~ + (C^mf + nF)/2 from f~;
+ *   LBE_SD_EU: f only, f* = f + (f_eq - f)/tau + S_f, J = sum c f;
+ *   LBE_DD_EU: f and g with the Euler update, J = sum c g, Pi = sum g.
+ * In the SD schemes g is not evolved; it holds a copy of f.  The adjoint
+ * (lbe_adjoint_flux_gradient) is that of LBE_DD_TR only. */
 typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_scheme;
 
 /* Optional device allocator.  alloc returns device memory of at least `bytes`
@@ -80,13 +87,14 @@ typedef struct {
     int periodic[3];          /* 1 = periodic axis; 0 = closed (outside = wall)  */
     int nspecies;             /* M, 1..4                                         */
     lbe_precision precision;
-    lbe_scheme scheme;        /* LBE_DD_TR                                       */
+    lbe_scheme scheme;        /* LBE_DD_TR, or an ablation (see lbe_scheme)      */
     int enable_visc;          /* C^{alpha,visc} (Appendix): must be 0             */
     int consistent_moments;   /* 0 (default): moments as printed in Sec. "Hard
                                  sphere fluid mixture": J = J~ + (C^mf + nF)/2,
                                  Pi = Pi~ - C^mf.u^alpha/2.  1: the map
                                  g = g~ + Omega/2 applied to the printed S_g:
-                                 J = J~ + nF/2, Pi = Pi~ + beta C^mf.u^alpha/2. */
+                                 J = J~ + nF/2, Pi = Pi~ + beta C^mf.u^alpha/2.
+                                 LBE_DD_TR only (LBE_ERR_INVALID_ARG otherwise). */
     int check_every;          /* > 0: lbe_step checks the device error word every
                                  this many steps (one stream sync each); 0: only
                                  getters check                                   */

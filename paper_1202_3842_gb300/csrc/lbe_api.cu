@@ -388,10 +388,12 @@ StepParams step_params(const lbe_ctx *c) {
     sp.consistent = c->cfg.consistent_moments ? 1 : 0;
     sp.flux_axis = c->flux_plane >= 0 ? c->flux_axis : -1;
     sp.flux_plane = c->flux_plane;
+    sp.scheme = c->cfg.scheme;
+    const bool euler = c->cfg.scheme == LBE_SD_EU || c->cfg.scheme == LBE_DD_EU;
     for (int a = 0; a < c->M; ++a) {
         double omega = 1.0 / (c->tau[a] - 0.5);
-        sp.sp[a].omega_eff = omega / (1.0 + 0.5 * omega);
-        sp.sp[a].inv = 1.0 / (1.0 + 0.5 * omega);
+        sp.sp[a].omega_eff = omega / (1.0 + 0.5 * omega);  // = 1/tau, also the Euler rate
+        sp.sp[a].inv = euler ? 1.0 : 1.0 / (1.0 + 0.5 * omega);
         sp.sp[a].n0 = c->n0[a];
     }
     return sp;
@@ -478,20 +480,33 @@ lbe_status state_moments(lbe_ctx *c, double **n, double **J) {
     *n = (double *)c->scratch64.p;
     *J = *n + (long long)c->M * N;
     StepParams sp = step_params(c);
-    LAUNCH(launch_moments(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, *n, *J,
-                          c->stream),
-           "moments kernel");
+    if (sp.scheme == LBE_DD_TR) {
+        LAUNCH(launch_moments(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, *n,
+                              *J, c->stream),
+               "moments kernel");
+    } else {
+        LAUNCH(launch_moments_ablation(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p,
+                                       sp, *n, *J, c->stream),
+               "ablation moments kernel");
+    }
     return LBE_OK;
 }
 
-// One DD-TR step of the current populations (K1-K3, K4, and K5 when psize > 0).
+// One step of the current populations (K1-K3, K4 of the configured scheme, and K5 when psize > 0).
 lbe_status step_once(lbe_ctx *c, const StepParams &sp, int psize) {
     TRY(force_stage(c));
     {
         StageTimer tm(c, LBE_STAGE_COLLIDE);
-        LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
-                              c->solid_links, c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
-               "collide kernel");
+        if (sp.scheme == LBE_DD_TR) {
+            LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
+                                  c->solid_links, c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
+                   "collide kernel");
+        } else {
+            LAUNCH(launch_collide_ablation(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p,
+                                           (const uint32_t *)c->mask.p, c->solid_links, c->C.p, c->F.p, sp,
+                                           (double *)c->flux_buf.p, c->stream),
+                   "ablation collide kernel");
+        }
     }
     c->cur = 1 - c->cur;
     if (psize > 0) {
@@ -541,7 +556,15 @@ lbe_status lbe_create(const lbe_config *cfg, const lbe_allocator *allocator, voi
     if (cfg->nspecies < 1 || cfg->nspecies > MAXS) return fail(nullptr, LBE_ERR_INVALID_ARG, "nspecies must be 1..4");
     if (cfg->precision < LBE_FP64 || cfg->precision > LBE_FP16_SHIFTED)
         return fail(nullptr, LBE_ERR_INVALID_ARG, "unknown precision");
-    if (cfg->scheme != LBE_DD_TR) return fail(nullptr, LBE_ERR_UNSUPPORTED, "only the DD-TR scheme is implemented");
+    if (cfg->scheme < LBE_DD_TR || cfg->scheme > LBE_DD_EU) return fail(nullptr, LBE_ERR_INVALID_ARG, "unknown scheme");
+    if (cfg->scheme != LBE_DD_TR) {
+        const Prec pr = cfg->precision == LBE_FP64 ? Prec::F64 : (cfg->precision == LBE_FP32 ? Prec::F32 : Prec::BF16);
+        if (!ablation_supported(pr, cfg->nspecies))
+            return fail(nullptr, LBE_ERR_UNSUPPORTED,
+                        "the SD-TR, SD-EU and DD-EU ablations run on FP64 or FP32 populations with one or two species");
+        if (cfg->consistent_moments)
+            return fail(nullptr, LBE_ERR_INVALID_ARG, "consistent_moments applies to the DD-TR scheme only");
+    }
     if (cfg->enable_visc) return fail(nullptr, LBE_ERR_UNSUPPORTED, "the viscous Enskog force is not implemented");
     if (allocator && (!allocator->alloc || !allocator->free))
         return fail(nullptr, LBE_ERR_INVALID_ARG, "allocator needs both alloc and free");
@@ -1083,6 +1106,7 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     if (plane < 0 || plane >= extent) return fail(c, LBE_ERR_INVALID_ARG, "plane index out of range");
     if (!(c->prec == Prec::F32 || c->prec == Prec::F64))
         return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint runs on FP64 or FP32 populations only");
+    if (c->cfg.scheme != LBE_DD_TR) return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint is that of the DD-TR scheme");
     TRY(prepare(c));
     const bool f64 = prec_fp64(c->prec);
     const size_t rb = real_bytes(c);

@@ -24,6 +24,7 @@ struct SpeciesConst {
 
 struct StepParams {
     int M;
+    int scheme;          // lbe_scheme: DD_TR (k_collide) or an ablation (k_collide_ablation)
     int consistent;      // moment recovery: 0 printed, 1 map-consistent
     int flux_axis;       // -1: no flux plane
     int flux_plane;
@@ -99,6 +100,13 @@ void shell_box(bool fp64, int S, int *bx, int *by);
 cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf,
                            cudaStream_t st);
+// Scheme ablations SD-TR, SD-EU, DD-EU (lbe_ablation.cu): FP64/FP32 storage, one or two species.
+bool ablation_supported(Prec p, int M);
+cudaError_t launch_collide_ablation(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask,
+                                    bool solid, const void *C, const void *F, const StepParams &sp,
+                                    double *flux_buf, cudaStream_t st);
+cudaError_t launch_moments_ablation(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *C,
+                                    const void *F, const StepParams &sp, double *n, double *J, cudaStream_t st);
 // Moments of the current state (FP64 out): n [M][N], J [M][3][N].
 cudaError_t launch_moments(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *C,
                            const void *F, const StepParams &sp, double *n, double *J, cudaStream_t st);

@@ -164,15 +164,18 @@ def current_stream_handle():
 # --------------------------------------------------------------------------
 # C ABI, one function each
 # --------------------------------------------------------------------------
+SCHEMES = {"dd_tr": LBE_DD_TR, "sd_tr": LBE_SD_TR, "sd_eu": LBE_SD_EU, "dd_eu": LBE_DD_EU}
+
+
 def lbe_create(shape, periodic=(1, 1, 1), nspecies=1, precision="fp32", consistent_moments=0, check_every=0,
-               allocator=None, stream=None):
+               allocator=None, stream=None, scheme="dd_tr"):
     cfg = lbe_config()
     cfg.nx, cfg.ny, cfg.nz = [int(v) for v in shape]
     for k in range(3):
         cfg.periodic[k] = int(bool(periodic[k]))
     cfg.nspecies = int(nspecies)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    cfg.scheme = LBE_DD_TR
+    cfg.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
     cfg.enable_visc = 0
     cfg.consistent_moments = int(bool(consistent_moments))
     cfg.check_every = int(check_every)
@@ -382,7 +385,7 @@ class Simulation:
     """One lattice on the current CUDA device; every method is one C ABI call."""
 
     def __init__(self, shape, periodic=(1, 1, 1), nspecies=1, precision="fp32", consistent_moments=False,
-                 check_every=0, use_torch_allocator=True, stream=None):
+                 check_every=0, use_torch_allocator=True, stream=None, scheme="dd_tr"):
         self.shape = tuple(int(v) for v in shape)
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
         self.M = int(nspecies)
@@ -393,7 +396,7 @@ class Simulation:
         if stream is None and use_torch_allocator:
             stream = current_stream_handle()
         self._h = lbe_create(self.shape, periodic, nspecies, precision, consistent_moments, check_every,
-                             self._alloc, stream)
+                             self._alloc, stream, scheme)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -17,11 +17,14 @@ def case_channel(shape, sigmas, eta, taus, width, length, body=1e-6, wall_amp_kT
     return w, inputs.build_workload(w)
 
 
-def setup_gpu(w, arrays, precision, consistent=False, check_every=0):
+SCHEME_IDS = {"dd_tr": 0, "sd_tr": 1, "sd_eu": 2, "dd_eu": 3}
+
+
+def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_tr"):
     from paper_1202_3842_gb300 import lbe
     M = len(w["sigma"])
     sim = lbe.Simulation(w["shape"], w["periodic"], M, precision, consistent_moments=consistent,
-                         check_every=check_every)
+                         check_every=check_every, scheme=scheme)
     sim.set_geometry(arrays["solid"])
     for a in range(M):
         sim.set_species(a, w["sigma"][a], w["tau"][a])
@@ -33,11 +36,12 @@ def setup_gpu(w, arrays, precision, consistent=False, check_every=0):
     return sim
 
 
-def setup_oracle(w, arrays, consistent=False):
+def setup_oracle(w, arrays, consistent=False, scheme="dd_tr"):
     M = len(w["sigma"])
     sim = oracle.Sim(w["shape"], w["periodic"], M)
     sim.set_geometry(arrays["solid"])
     sim.set_consistent_moments(consistent)
+    sim.set_scheme(SCHEME_IDS[scheme])
     for a in range(M):
         sim.set_species(a, w["sigma"][a], w["tau"][a])
         sim.set_potential(a, arrays["V"][a])

@@ -64,3 +64,19 @@ def test_bad_config_is_rejected_before_device_use(L):
     cfg.nspecies = 1
     cfg.enable_visc = 1
     assert L.lbe_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == 2
+
+
+def test_scheme_config_is_checked_before_device_use(L):
+    def create(**kw):
+        cfg = lbe.lbe_config()
+        cfg.nx, cfg.ny, cfg.nz = 4, 4, 4
+        cfg.nspecies = kw.get("M", 1)
+        cfg.precision = kw.get("prec", lbe.LBE_FP32)
+        cfg.scheme = kw.get("scheme", lbe.LBE_DD_TR)
+        cfg.consistent_moments = kw.get("consistent", 0)
+        out = ctypes.c_void_p()
+        return L.lbe_create(ctypes.byref(cfg), None, None, ctypes.byref(out))
+    assert create(scheme=7) == 1                                          # unknown scheme
+    assert create(scheme=lbe.LBE_SD_EU, prec=lbe.LBE_BF16_SHIFTED) == 2   # ablations: FP64/FP32 only
+    assert create(scheme=lbe.LBE_SD_TR, M=3) == 2                         # ablations: one or two species
+    assert create(scheme=lbe.LBE_DD_EU, consistent=1) == 1                # consistent recovery is DD-TR's
