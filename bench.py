@@ -178,7 +178,7 @@ def source_hash(files):
 
 
 KERNEL_SOURCES = {
-    "collide": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh",
+    "collide": ["paper_1202_3842_gb300/csrc/lbe_collide_pair.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh",
                 "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
     "shell": ["paper_1202_3842_gb300/csrc/lbe_shell.cu", "paper_1202_3842_gb300/csrc/lbe_shell.cuh",
               "paper_1202_3842_gb300/csrc/lbe_shell_kernels.cuh", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
@@ -404,7 +404,8 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
         alg = N * M * 4 * QPOP * sb  # populations f~ and g~ read + written
         achieved = alg / (per_launch_ms * 1e-3) / 1e9
         peak = float(peaks["hbm_gbs"])
-        roof = {"kernel": "k_collide (K4 fused moments + DD-TR collision + streaming)", "bound": "hbm",
+        kname = "k_collide_pair" if M <= 2 else "k_collide"
+        roof = {"kernel": kname + " (K4 fused moments + DD-TR collision + streaming)", "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic_for("collide", wname, prec), "algorithmic_bytes_per_launch": alg,
                 "launches": dom_n, "avg_launch_ms": per_launch_ms,

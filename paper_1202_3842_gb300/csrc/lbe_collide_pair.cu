@@ -1,0 +1,172 @@
+// K4 for one or two species with species-parallel lanes: fused moments +
+// DD-TR collision + pull streaming (Sec. "Hard sphere fluid mixture in a
+// potential well"; the arithmetic is that of k_collide in lbe_kernels.cu).
+//
+// Two species: lanes 0-15 of a warp take species 0 and lanes 16-31 species 1
+// of the same 16 consecutive nodes.  Each thread pulls only its own species'
+// 38 populations and keeps them in registers, computes that species' moments,
+// and gets the partner species' n and J from lane ^ 16 by a shuffle to form the
+// barycentric velocity u = (J_0 + J_1)/(n_0 + n_1).  A warp's load of one
+// population is two 64-byte runs, whole 32-byte sectors.  Compared with one
+// thread per node holding both species, the live state per thread halves,
+// which lets three CTAs of 256 threads share an SM.  One species: one thread
+// per node, 32 consecutive nodes per warp, u = J/n.
+#include <math.h>
+
+#include <utility>
+
+#include "lbe_device.cuh"
+#include "lbe_launch.h"
+#include "lbe_node.cuh"
+
+namespace lbe {
+
+constexpr int NTP = 256;  // threads per CTA: 128 nodes (two species) or 256 (one)
+
+template <typename S, typename T, int M, bool SOLID>
+__global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? 3 : 1)
+    k_collide_pair(Grid g, const S *__restrict__ src, S *__restrict__ dst, const uint32_t *__restrict__ mask,
+                   const T *__restrict__ C, const T *__restrict__ F, StepParams sp, double *__restrict__ flux_buf) {
+    static_assert(M == 1 || M == 2, "one or two species");
+    const int lane = threadIdx.x & 31;
+    const int a = M == 2 ? lane >> 4 : 0;  // species of this thread
+    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x >> 5) * 16 + (lane & 15)
+                               : (long long)blockIdx.x * NTP + threadIdx.x;
+    const bool valid = i < g.N;
+    int x = 0, y = 0, z = 0;
+    if (valid) node_xyz(g, i, x, y, z);
+    const uint32_t m = valid ? (SOLID ? mask[i] : 0u) : 1u;
+    const bool fluid = !(m & 1u);
+    const int coord = sp.flux_axis == 0 ? x : (sp.flux_axis == 1 ? y : z);
+    const bool on_plane = valid && sp.flux_axis >= 0 && coord == sp.flux_plane;
+    const int psize = sp.flux_axis == 0 ? g.ny * g.nz : (sp.flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
+
+    // this species' constants (selected, not indexed, so the parameter block stays in constant memory)
+    const double n0d = a == 0 ? sp.sp[0].n0 : sp.sp[1].n0;
+    const double omd = a == 0 ? sp.sp[0].omega_eff : sp.sp[1].omega_eff;
+    const double invd = a == 0 ? sp.sp[0].inv : sp.sp[1].inv;
+    // moments of this thread's species (zero on solid nodes and past the end)
+    T f[Q], gq[Q];
+    T n = 0, Pi = 0, J[3] = {0, 0, 0}, Cv[3] = {0, 0, 0}, nF[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+    NbrOff o{};
+    if (fluid) {
+        o = nbr_offsets(g, x, y, z);
+        const T n0 = (T)n0d;
+        const S *fb = src + pop_off(a, 0, 0, g.N);
+        const S *gb = src + pop_off(a, 1, 0, g.N);
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            ((f[P] = pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+            ((gq[P] = pull<S, T, P, SOLID>(gb, g.N, i, o, m, n0)), ...);
+        }(std::make_integer_sequence<int, Q>{});
+        T Pit = 0, Jt[3] = {0, 0, 0};
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            ((n += f[P]), ...);
+            ((Pit += gq[P]), ...);
+            ((Jt[0] += (T)cx(P) * gq[P]), ...);
+            ((Jt[1] += (T)cy(P) * gq[P]), ...);
+            ((Jt[2] += (T)cz(P) * gq[P]), ...);
+        }(std::make_integer_sequence<int, Q>{});
+        const T inv_n = n > (T)0 ? (T)1 / n : (T)0;
+        T Cu = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Cv[c] = C[((long long)a * 3 + c) * g.N + i];
+            nF[c] = n * F[((long long)a * 3 + c) * g.N + i];
+            J[c] = sp.consistent ? Jt[c] + (T)0.5 * nF[c] : Jt[c] + (T)0.5 * (Cv[c] + nF[c]);
+            ua[c] = J[c] * inv_n;
+            Cu += Cv[c] * ua[c];
+        }
+        Pi = sp.consistent ? Pit + (T)1.5 * Cu : Pit - (T)0.5 * Cu;
+    }
+    // the partner species (lane ^ 16) of the same node; every lane takes part
+    T np = 0, Jp[3] = {0, 0, 0};
+    if constexpr (M == 2) {
+        np = __shfl_xor_sync(0xffffffffu, n, 16);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Jp[c] = __shfl_xor_sync(0xffffffffu, J[c], 16);
+    }
+    if (on_plane)
+        flux_buf[(long long)a * psize + plane_index(g, sp.flux_axis, x, y, z)] =
+            fluid ? (double)J[sp.flux_axis] : 0.0;
+    if (!fluid) return;
+    // species order in the sums: n_0 + n_1, J_0 + J_1 (one species: 0 + n, 0 + J as in k_collide)
+    const T ntot = a == 0 ? n + np : np + n;
+    const T inv_tot = ntot > (T)0 ? (T)1 / ntot : (T)0;
+    T u[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = (a == 0 ? J[c] + Jp[c] : Jp[c] + J[c]) * inv_tot;
+
+    const T uau = ua[0] * u[0] + ua[1] * u[1] + ua[2] * u[2];
+    const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    const T iso = (T)1.5 * n * ((T)2 * uau - uu);
+    const T A = n - iso;
+    const T B = Pi - iso;
+    T X[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) X[c] = Cv[c] + nF[c];
+    const T sf0 = (T)-3 * (X[0] * ua[0] + X[1] * ua[1] + X[2] * ua[2]);
+    const T om = (T)omd;
+    const T inv = (T)invd;
+    const T in0 = n0d > 0.0 ? (T)(1.0 / n0d) : (T)0;
+    S *fo = dst + pop_off(a, 0, 0, g.N) + i;
+    S *go = dst + pop_off(a, 1, 0, g.N) + i;
+    [&]<int... P>(std::integer_sequence<int, P...>) {
+        (
+            [&] {
+                constexpr T w = (T)wq(P);
+                const T cua = cdot<T, P>(ua);
+                const T cu = cdot<T, P>(u);
+                const T cX = cdot<T, P>(X);
+                const T cY = cdot<T, P>(nF);
+                const T cC = cdot<T, P>(Cv);
+                const T t1 = (T)3 * n * cua + (T)4.5 * n * ((T)2 * cua * cu - cu * cu);
+                const T feq = w * (A + t1);
+                const T geq = w * (B + t1);
+                const T Sf = w * (sf0 + (T)3 * cX + (T)9 * cX * cua);
+                const T Sg = w * (sf0 + (T)3 * cY + (T)18 * cC * cua + (T)9 * cY * cua);
+                const T fs = f[P] + om * (feq - f[P]) + inv * Sf;
+                const T gs = gq[P] + om * (geq - gq[P]) + inv * Sg;
+                constexpr T iw = (T)(1.0 / wq(P));
+                Store<S, T>::store(fo + (long long)P * g.N, fs, iw * in0);
+                Store<S, T>::store(go + (long long)P * g.N, gs, iw * in0);
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, Q>{});
+}
+
+#define LBE_PAIR_DISPATCH(p, ...)                                                      \
+    switch (p) {                                                                       \
+        case Prec::F64: { using S = double; using T = double; __VA_ARGS__; break; }    \
+        case Prec::F32: { using S = float; using T = float; __VA_ARGS__; break; }      \
+        case Prec::BF16: { using S = __nv_bfloat16; using T = float; __VA_ARGS__; break; } \
+        case Prec::F16: { using S = __half; using T = float; __VA_ARGS__; break; }     \
+    }
+
+cudaError_t launch_collide_pair(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
+                                const void *C, const void *F, const StepParams &sp, double *flux_buf,
+                                cudaStream_t st) {
+    const int per_cta = sp.M == 2 ? NTP / 2 : NTP;
+    const unsigned nb = (unsigned)((g.N + per_cta - 1) / per_cta);
+#define LBE_PAIR(MM, SOL)                                                                                   \
+    k_collide_pair<S, T, MM, SOL><<<nb, NTP, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C,      \
+                                                      (const T *)F, sp, flux_buf)
+    if (sp.M == 1) {
+        if (solid) {
+            LBE_PAIR_DISPATCH(p, LBE_PAIR(1, true));
+        } else {
+            LBE_PAIR_DISPATCH(p, LBE_PAIR(1, false));
+        }
+    } else if (sp.M == 2) {
+        if (solid) {
+            LBE_PAIR_DISPATCH(p, LBE_PAIR(2, true));
+        } else {
+            LBE_PAIR_DISPATCH(p, LBE_PAIR(2, false));
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef LBE_PAIR
+    return cudaGetLastError();
+}
+
+}  // namespace lbe

@@ -406,9 +406,7 @@ static cudaError_t collide_m(int M, const Grid &g, const void *src, void *dst, c
 #define LBE_COLLIDE(MM)                                                                                   \
     k_collide<S, T, MM, SOLID><<<nb, NT, 0, st>>>(g, (const S *)src, (S *)dst, mask, (const T *)C, (const T *)F, \
                                                   sp, flux_buf)
-    switch (M) {
-        case 1: LBE_COLLIDE(1); break;
-        case 2: LBE_COLLIDE(2); break;
+    switch (M) {  // one or two species: k_collide_pair (lbe_collide_pair.cu)
         case 3: LBE_COLLIDE(3); break;
         case 4: LBE_COLLIDE(4); break;
         default: return cudaErrorInvalidValue;
@@ -419,6 +417,7 @@ static cudaError_t collide_m(int M, const Grid &g, const void *src, void *dst, c
 
 cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf, cudaStream_t st) {
+    if (sp.M <= 2) return launch_collide_pair(p, g, src, dst, mask, solid, C, F, sp, flux_buf, st);
     cudaError_t e = cudaSuccess;
     if (solid) {
         LBE_DISPATCH_PREC(p, (e = collide_m<S, T, true>(sp.M, g, src, dst, mask, C, F, sp, flux_buf, st)));
