@@ -468,12 +468,12 @@ cudaError_t launch_adj_tile(const AdjShellTile &L, cudaStream_t st);
 cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st) {
     if (!fp64) {
         switch (S) {
-            case 1: return launch_adj_tile<float, 1, 2, 16>(L, st);
-            case 2: return launch_adj_tile<float, 2, 2, 16>(L, st);
-            case 3: return launch_adj_tile<float, 3, 2, 16>(L, st);
-            case 4: return launch_adj_tile<float, 4, 2, 16>(L, st);
-            case 5: return launch_adj_tile<float, 5, 2, 16>(L, st);
-            case 6: return launch_adj_tile<float, 6, 2, 16>(L, st);
+            case 1: return launch_adj_tile<float, 1, 3, 16>(L, st);
+            case 2: return launch_adj_tile<float, 2, 3, 16>(L, st);
+            case 3: return launch_adj_tile<float, 3, 3, 16>(L, st);
+            case 4: return launch_adj_tile<float, 4, 3, 16>(L, st);
+            case 5: return launch_adj_tile<float, 5, 3, 16>(L, st);
+            case 6: return launch_adj_tile<float, 6, 3, 16>(L, st);
             case 7: return launch_adj_tile<float, 7, 2, 16>(L, st);
             case 8: return launch_adj_tile<float, 8, 1, 8>(L, st);
             default: return cudaErrorInvalidValue;

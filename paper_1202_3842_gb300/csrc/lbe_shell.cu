@@ -1,7 +1,8 @@
 // Dispatch of the shell-force kernels by precision and pair diameter, and the
 // host-side shell helpers.  FP32 pair diameters up to 7 use the z-blocked
-// kernel (two outputs per thread along z, 32 x 16 threads); diameter 8 and the
-// FP64 path use the plain kernel (one output per thread and plane).  The kernels are instantiated in lbe_shell_f32_*.cu
+// kernel (32 x 16 threads; three outputs per thread along z up to diameter 6,
+// two at 7, where three would not fit the shared-memory ring); diameter 8 and
+// the FP64 path use the plain kernel (one output per thread and plane).  The kernels are instantiated in lbe_shell_f32_*.cu
 // and lbe_shell_f64.cu.
 #include "lbe_device.cuh"
 #include "lbe_launch.h"
@@ -19,12 +20,12 @@ cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st);
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st) {
     if (!fp64) {
         switch (S) {
-            case 1: return launch_zb<float, 1, 2, 16>(L, st);
-            case 2: return launch_zb<float, 2, 2, 16>(L, st);
-            case 3: return launch_zb<float, 3, 2, 16>(L, st);
-            case 4: return launch_zb<float, 4, 2, 16>(L, st);
-            case 5: return launch_zb<float, 5, 2, 16>(L, st);
-            case 6: return launch_zb<float, 6, 2, 16>(L, st);
+            case 1: return launch_zb<float, 1, 3, 16>(L, st);
+            case 2: return launch_zb<float, 2, 3, 16>(L, st);
+            case 3: return launch_zb<float, 3, 3, 16>(L, st);
+            case 4: return launch_zb<float, 4, 3, 16>(L, st);
+            case 5: return launch_zb<float, 5, 3, 16>(L, st);
+            case 6: return launch_zb<float, 6, 3, 16>(L, st);
             case 7: return launch_zb<float, 7, 2, 16>(L, st);
             case 8: return launch_one<float, 8>(L, st);
             default: return cudaErrorInvalidValue;

@@ -132,7 +132,7 @@ struct ShellTileZ {
     static constexpr int PLANE_BYTES = ((PLANE * (int)sizeof(T)) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = 2 * PLANE_BYTES;
     static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
-    static constexpr int LZ = 16;  // multiple of TZ
+    static constexpr int LZ = TZ == 3 ? 18 : 16;  // planes per CTA, a multiple of TZ
 };
 
 }  // namespace lbe

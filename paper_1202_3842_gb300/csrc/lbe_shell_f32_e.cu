@@ -1,0 +1,6 @@
+// Explicit instantiations of the FP32 shell-force kernels.
+#include "lbe_shell_kernels.cuh"
+
+namespace lbe {
+template cudaError_t launch_zb<float, 6, 3, 16>(const ShellLaunch &, cudaStream_t);
+}  // namespace lbe
