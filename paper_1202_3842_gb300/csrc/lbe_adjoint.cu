@@ -11,7 +11,8 @@
 //   K3^T  k_adj_shell_prep / k_adj_shell_tile   shell force transposed: node-local
 //                         terms, then divergence-type shell sums of the weighted
 //                         adjoint from shared-memory tiles (lbe_adj_shell.cuh)
-//   K2^T  k_adj_contact_prep / k_adj_ball  BMCSL contact value and ball average transposed
+//   K2^T  k_adj_contact_prep / k_contact_tma<MODE 1>  BMCSL contact value and ball
+//                         average transposed
 //   K1^T  the density adjoint is kept as a field and added in the next push-gather
 // All arithmetic in the precision T of the populations (FP32 or FP64).
 #include <utility>
@@ -309,33 +310,20 @@ __global__ void k_adj_shell_prep(Grid g, const T *__restrict__ npad_a, const T *
 }
 
 // ---------------------------------------------------------------------------
-// Contact value and ball average transposed.
+// Contact value transposed (first half; the ball average's transpose is the
+// TMA ball sum of lbe_adj_ball.cu).  From the xi2, xi3 kept by the forward
+// contact kernel:
 //   lxi2 = sum_ab lg_ab dg_ab/dxi2, lxi3 = sum_ab lg_ab dg_ab/dxi3,
-//   lnbar_b = (pi/6)(sigma_b^2 lxi2 + sigma_b^3 lxi3) / |B_b|  (padded),
-//   ln_b(r) += sum_{|d| <= sigma_b/2} lnbar_b(r + d)   (the ball is symmetric)
+//   lnbar_b = (pi/6)(sigma_b^2 lxi2 + sigma_b^3 lxi3) / |B_b|  (padded).
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_adj_contact_prep(Grid g, ContactParams cp, BallRows br, const T *__restrict__ npad,
+__global__ void k_adj_contact_prep(Grid g, ContactParams cp, BallRows br, const T *__restrict__ xi,
                                    const T *__restrict__ lg, T *__restrict__ lnbar) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
-    const long long pc = pidx(g, x, y, z);
-    T xi2 = 0, xi3 = 0;
-    for (int b = 0; b < cp.M; ++b) {
-        T acc = 0;
-        for (int dz = -4; dz <= 4; ++dz) {
-            const int k0 = br.first[b][dz + 4], k1 = br.first[b][dz + 5];
-            for (int k = k0; k < k1; ++k) {
-                const long long row = pc + (long long)g.px * ((long long)br.dy[b][k] + (long long)g.py * dz);
-                for (int dx = -br.a[b][k]; dx <= br.a[b][k]; ++dx) acc += npad[(long long)b * g.P + row + dx];
-            }
-        }
-        const T nbar = acc / (T)br.count[b];
-        xi2 += (T)cp.xi2c[b] * nbar;
-        xi3 += (T)cp.xi3c[b] * nbar;
-    }
+    const T xi2 = xi[i], xi3 = xi[g.N + i];
     const T i1 = (T)1 / ((T)1 - xi3);
     T l2 = 0, l3 = 0;
     for (int a = 0; a < cp.M; ++a)
@@ -348,29 +336,6 @@ __global__ void k_adj_contact_prep(Grid g, ContactParams cp, BallRows br, const 
     for (int b = 0; b < cp.M; ++b) {
         const T v = ((T)cp.xi2c[b] * l2 + (T)cp.xi3c[b] * l3) / (T)br.count[b];
         write_padded<T>(g, lnbar + (long long)b * g.P, x, y, z, v);
-    }
-}
-
-template <typename T>
-__global__ void k_adj_ball(Grid g, int M, BallRows br, const uint32_t *__restrict__ mask,
-                           const T *__restrict__ lnbar, T *__restrict__ ln) {
-    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.N) return;
-    int x, y, z;
-    node_xyz(g, i, x, y, z);
-    const long long pc = pidx(g, x, y, z);
-    const bool solid = mask[i] & 1u;
-    for (int b = 0; b < M; ++b) {
-        T acc = 0;
-        for (int dz = -4; dz <= 4; ++dz) {
-            const int k0 = br.first[b][dz + 4], k1 = br.first[b][dz + 5];
-            for (int k = k0; k < k1; ++k) {
-                const long long row = pc + (long long)g.px * ((long long)br.dy[b][k] + (long long)g.py * dz);
-                for (int dx = -br.a[b][k]; dx <= br.a[b][k]; ++dx) acc += lnbar[(long long)b * g.P + row + dx];
-            }
-        }
-        T *o = ln + (long long)b * g.N + i;
-        *o = solid ? (T)0 : *o + acc;  // the density of a solid node is fixed at zero
     }
 }
 
@@ -491,19 +456,15 @@ cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaS
     }
 }
 
-cudaError_t launch_adj_contact(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
-                               const uint32_t *mask, const void *npad, const void *lg, void *lnbar, void *ln,
-                               cudaStream_t st) {
+cudaError_t launch_adj_contact_prep(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
+                                   const void *xi, const void *lg, void *lnbar, cudaStream_t st) {
     const unsigned nb = (unsigned)((g.N + ANT - 1) / ANT);
-    if (fp64) {
-        k_adj_contact_prep<double><<<nb, ANT, 0, st>>>(g, cp, br, (const double *)npad, (const double *)lg,
+    if (fp64)
+        k_adj_contact_prep<double><<<nb, ANT, 0, st>>>(g, cp, br, (const double *)xi, (const double *)lg,
                                                        (double *)lnbar);
-        k_adj_ball<double><<<nb, ANT, 0, st>>>(g, cp.M, br, mask, (const double *)lnbar, (double *)ln);
-    } else {
-        k_adj_contact_prep<float><<<nb, ANT, 0, st>>>(g, cp, br, (const float *)npad, (const float *)lg,
+    else
+        k_adj_contact_prep<float><<<nb, ANT, 0, st>>>(g, cp, br, (const float *)xi, (const float *)lg,
                                                       (float *)lnbar);
-        k_adj_ball<float><<<nb, ANT, 0, st>>>(g, cp.M, br, mask, (const float *)lnbar, (float *)ln);
-    }
     return cudaGetLastError();
 }
 

@@ -229,18 +229,23 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
     return fn;
 }
 
-lbe_status make_map(lbe_ctx *c, CUtensorMap *map, void *base, int bx, int by) {
+// 3-D map over a padded field of the compute type, or (pair = true, FP32) over the interleaved
+// (n_b, g_ab n_b) field as 8-byte elements.
+lbe_status make_map(lbe_ctx *c, CUtensorMap *map, void *base, int bx, int by, bool pair = false) {
     auto enc = get_encode();
     if (!enc) return fail(c, LBE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const bool f64 = prec_fp64(c->prec);
-    const size_t es = f64 ? 8 : 4;
+    const bool e8 = f64 || pair;
+    const size_t es = e8 ? 8 : 4;
     cuuint64_t dims[3] = {(cuuint64_t)c->g.px, (cuuint64_t)c->g.py, (cuuint64_t)c->g.pz};
     cuuint64_t strides[2] = {(cuuint64_t)c->g.px * es, (cuuint64_t)c->g.px * c->g.py * es};
     cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims,
-                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const CUtensorMapDataType dt = f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
+                                       : (pair ? CU_TENSOR_MAP_DATA_TYPE_UINT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+    CUresult r = enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(c, LBE_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
     return LBE_OK;
 }
@@ -346,19 +351,21 @@ lbe_status prepare(lbe_ctx *c) {
         c->cparams = cp;
         const size_t rb = real_bytes(c);
         TRY(dev_alloc(c, c->npad, rb * c->M * g.P));
-        TRY(dev_alloc(c, c->gnpad, rb * c->M * c->M * g.P));
+        // g_ab n_b of every ordered pair: FP32 stores the interleaved pair (n_b, g_ab n_b), 8 bytes per node
+        const size_t gnb = (f64 ? rb : 2 * rb) * c->M * c->M * g.P;
+        TRY(dev_alloc(c, c->gnpad, gnb));
         TRY(dev_alloc(c, c->gab, rb * c->M * c->M * g.N));
         TRY(dev_alloc(c, c->C, rb * c->M * 3 * g.N));
         CK(cudaMemsetAsync(c->npad.p, 0, rb * c->M * g.P, c->stream), "memset npad");
-        CK(cudaMemsetAsync(c->gnpad.p, 0, rb * c->M * c->M * g.P, c->stream), "memset gnpad");
+        CK(cudaMemsetAsync(c->gnpad.p, 0, gnb, c->stream), "memset gnpad");
         CK(cudaMemsetAsync(c->C.p, 0, rb * c->M * 3 * g.N, c->stream), "memset C");
         for (auto &ps : c->pairs) {
             char *nb = (char *)c->npad.p + rb * ps.b * g.P;
-            char *gn = (char *)c->gnpad.p + rb * (ps.a * c->M + ps.b) * g.P;
+            char *gn = (char *)c->gnpad.p + (f64 ? rb : 2 * rb) * (ps.a * c->M + ps.b) * g.P;
             int bx = 0, by = 0;
             shell_box(f64, ps.S, &bx, &by);
-            TRY(make_map(c, &ps.map_n, nb, bx, by));
-            TRY(make_map(c, &ps.map_gn, gn, bx, by));
+            if (f64) TRY(make_map(c, &ps.map_n, nb, bx, by));
+            TRY(make_map(c, &ps.map_gn, gn, bx, by, !f64));
         }
         {
             int bx = 0, by = 0;
@@ -401,8 +408,9 @@ StepParams step_params(const lbe_ctx *c) {
 
 // K1 -> K2 -> K3 for the populations pop (default: the current state); fills
 // npad, gab, gnpad, C.  With Pbase, the shell kernels also store P of every
-// pair into Pbase [npairs][3][N] (for the adjoint).
-lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = nullptr) {
+// pair into Pbase [npairs][3][N], and with xibase the contact kernel stores
+// xi2, xi3 into xibase [2][N] (both for the adjoint).
+lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = nullptr, void *xibase = nullptr) {
     const bool f64 = prec_fp64(c->prec);
     const size_t rb = real_bytes(c);
     if (!pop) pop = c->pop[c->cur].p;
@@ -423,6 +431,7 @@ lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = null
         L.RB = c->RB;
         L.gab = c->gab.p;
         L.gnpad = c->gnpad.p;
+        L.xi = xibase;
         L.err = (int *)c->err.p;
         LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
     }
@@ -1120,10 +1129,10 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
 
     // Device memory: checkpoints ck[s] (state at step s*K), the states 1..K-1 of the segment being
     // reversed (seg[k]), and per segment step the fields of its force stage (slot[k]): npad [M][P],
-    // gnpad [M][M][P], gab [M][M][N], C [M][3][N], P [npairs][3][N].
+    // gab [M][M][N], C [M][3][N], xi2 and xi3 [2][N], P [npairs][3][N].
     const int npairs = (int)c->pairs.size();
-    const size_t sl_npad = 0, sl_gnpad = sl_npad + rb * M * P, sl_gab = sl_gnpad + rb * M * M * P,
-                 sl_C = sl_gab + rb * M * M * N, sl_P = sl_C + rb * M * 3 * N,
+    const size_t sl_npad = 0, sl_gab = sl_npad + rb * M * P,
+                 sl_C = sl_gab + rb * M * M * N, sl_xi = sl_C + rb * M * 3 * N, sl_P = sl_xi + rb * 2 * N,
                  slot_bytes = sl_P + rb * 3 * (size_t)std::max(npairs, 1) * N;
     std::vector<Buf> ck(nseg), seg(kseg), slot(kseg);
     Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, lmom, outA, red;
@@ -1168,11 +1177,18 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     ATRY(alloc(outA, 8 * N, false));
     ATRY(alloc(red, 8 * N, false));
 
+    // tensor maps of the padded adjoint ball averages (box of the contact kernel)
+    std::vector<CUtensorMap> ballmaps(MAXS);
+    {
+        int bx = 0, by = 0;
+        contact_box(f64, M, c->RB, &bx, &by);
+        for (int b = 0; b < M; ++b) ATRY(make_map(c, &ballmaps[b], (char *)lnbar.p + rb * b * P, bx, by));
+    }
     // tensor maps of the padded Lambda_c and (g Lambda)_c with the box of each pair's shell
     std::vector<CUtensorMap> mapL(3 * npairs), mapgL(3 * npairs);
     for (int q = 0; q < npairs; ++q) {
         int bx = 0, by = 0;
-        shell_box(f64, c->pairs[q].S, &bx, &by);
+        adj_shell_box(f64, c->pairs[q].S, &bx, &by);
         for (int cc = 0; cc < 3; ++cc) {
             ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + rb * cc * P, bx, by));
             ATRY(make_map(c, &mapgL[3 * q + cc], (char *)gLpad.p + rb * cc * P, bx, by));
@@ -1216,14 +1232,11 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
         // recompute the segment: the force stage of every state (kept in its slot) and the states
         for (int k = 0; k < nst; ++k) {
             char *sl = (char *)slot[k].p;
-            ATRY(force_stage(c, state(k), npairs ? sl + sl_P : nullptr));
+            ATRY(force_stage(c, state(k), npairs ? sl + sl_P : nullptr, npairs ? sl + sl_xi : nullptr));
             CK(cudaMemcpyAsync(sl + sl_npad, c->npad.p, rb * M * P, cudaMemcpyDeviceToDevice, c->stream), "keep npad");
-            if (npairs) {
-                CK(cudaMemcpyAsync(sl + sl_gnpad, c->gnpad.p, rb * M * M * P, cudaMemcpyDeviceToDevice, c->stream),
-                   "keep gnpad");
+            if (npairs)
                 CK(cudaMemcpyAsync(sl + sl_gab, c->gab.p, rb * M * M * N, cudaMemcpyDeviceToDevice, c->stream),
                    "keep gab");
-            }
             CK(cudaMemcpyAsync(sl + sl_C, c->C.p, rb * M * 3 * N, cudaMemcpyDeviceToDevice, c->stream), "keep C");
             if (k + 1 < nst) {
                 StageTimer tm(c, LBE_STAGE_COLLIDE);
@@ -1271,10 +1284,18 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                 c->launches += 2;  // one launch per component
             }
             if (npairs) {
-                LAUNCH(launch_adj_contact(f64, c->g, c->cparams, c->brows, (const uint32_t *)c->mask.p,
-                                          sl + sl_npad, lg.p, lnbar.p, lnd[1 - cl].p, c->stream),
+                LAUNCH(launch_adj_contact_prep(f64, c->g, c->cparams, c->brows, sl + sl_xi, lg.p, lnbar.p, c->stream),
                        "adjoint contact");
-                c->launches += 1;
+                ContactLaunch LB{};
+                LB.grid = &c->g;
+                LB.maps = ballmaps.data();
+                LB.cp = &c->cparams;
+                LB.br = &c->brows;
+                LB.RB = c->RB;
+                LB.mask = (const uint32_t *)c->mask.p;
+                LB.ln = lnd[1 - cl].p;
+                LB.err = (int *)c->err.p;
+                LAUNCH(launch_adj_ball_tma(f64, LB, c->stream), "adjoint ball sum");
             }
             cl = 1 - cl;
         }

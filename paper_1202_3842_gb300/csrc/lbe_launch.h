@@ -57,6 +57,9 @@ struct ContactLaunch {
     int RB;                   // largest ball half-width
     void *gab;
     void *gnpad;
+    void *xi;                  // NULL, or [2][N]: xi2, xi3 (kept for the adjoint)
+    const uint32_t *mask;      // adjoint ball sum only
+    void *ln;                  // adjoint ball sum only: [M][N] accumulated
     int *err;
 };
 
@@ -91,11 +94,14 @@ cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_
                            const double *n0, void *npad, int *err, cudaStream_t st);
 // K2: ball averages, BMCSL contact values g_ab [M][M][N] and padded g_ab*n_b [M][M][P].
 cudaError_t launch_contact_tma(bool fp64, const ContactLaunch &L, cudaStream_t st);
+// Transposed ball average: L.maps over the padded adjoint fields lnbar; ln[b] += ball sum, 0 on solid nodes.
+cudaError_t launch_adj_ball_tma(bool fp64, const ContactLaunch &L, cudaStream_t st);
 void contact_box(bool fp64, int M, int RB, int *bx, int *by);
 // K3: shell force of one ordered pair.
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st);
 bool shell_supported(bool fp64, int S);
-void shell_box(bool fp64, int S, int *bx, int *by);
+void shell_box(bool fp64, int S, int *bx, int *by);      // forward: FP32 boxes count 8-byte (n, g n) elements
+void adj_shell_box(bool fp64, int S, int *bx, int *by);  // shell transpose: boxes of the compute type
 // K4: fused moments + DD-TR collision + pull streaming.
 cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf,
@@ -178,9 +184,8 @@ cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const ui
                                void *lmom /* [M][5][N] scratch */, cudaStream_t st);
 cudaError_t launch_adj_shell_prep(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st);
 cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st);
-cudaError_t launch_adj_contact(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
-                               const uint32_t *mask, const void *npad, const void *lg, void *lnbar, void *ln,
-                               cudaStream_t st);
+cudaError_t launch_adj_contact_prep(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,
+                                   const void *xi, const void *lg, void *lnbar, cudaStream_t st);
 cudaError_t launch_adj_amp(bool fp64, const Grid &g, int M, const void *lF, const double *phi, double *out,
                            cudaStream_t st);
 

@@ -135,4 +135,23 @@ struct ShellTileZ {
     static constexpr int LZ = TZ == 3 ? 18 : 16;  // planes per CTA, a multiple of TZ
 };
 
+// Tile of the FP32 z-blocked forward kernel on the interleaved field: one
+// 8-byte element (n_b, g_ab n_b) per node, so one shared load fetches both
+// values of a stencil point and the two sums run as packed f32x2 arithmetic.
+// TMA sees 8-byte elements: the x coordinate must be even (A = 2).
+template <int S, int TZ, int TYB = 16>
+struct ShellTileZ2 {
+    static constexpr int A = 2;
+    static constexpr int TX = 32;
+    static constexpr int TY = TYB;
+    static constexpr int BX = ((TX + 2 * S + A - 1) + A - 1) / A * A;
+    static constexpr int BY = TY + 2 * S;
+    static constexpr int R = 2 * S + 2 * TZ;
+    static constexpr int PLANE = BX * BY;  // 8-byte elements of one plane
+    static constexpr int PLANE_BYTES = ((PLANE * 8) + 127) / 128 * 128;
+    static constexpr int SLOT_BYTES = PLANE_BYTES;
+    static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
+    static constexpr int LZ = TZ == 3 ? 18 : 16;  // planes per CTA, a multiple of TZ
+};
+
 }  // namespace lbe

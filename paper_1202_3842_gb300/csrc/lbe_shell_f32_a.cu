@@ -2,8 +2,8 @@
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_zb<float, 1, 3, 16>(const ShellLaunch &, cudaStream_t);
-template cudaError_t launch_zb<float, 2, 3, 16>(const ShellLaunch &, cudaStream_t);
-template cudaError_t launch_zb<float, 3, 3, 16>(const ShellLaunch &, cudaStream_t);
-template cudaError_t launch_zb<float, 4, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<1, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<2, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<3, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<4, 3, 16>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

@@ -2,5 +2,5 @@
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_zb<float, 7, 2, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<7, 2, 16>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

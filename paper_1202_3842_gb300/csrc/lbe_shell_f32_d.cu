@@ -2,5 +2,5 @@
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_one<float, 8>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<8, 1, 8>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

@@ -9,12 +9,15 @@
 // with coef = -kT sigma_ab^2 w_ab.  Both sums run over the half shell as
 // e^ [a(r+e) - a(r-e)].
 //
-// Data path: the padded density n_b and the padded product g_ab*n_b are
-// streamed plane by plane (z-marching) into a shared-memory ring by TMA
-// (cp.async.bulk.tensor, one 2-D box of (32 + 2S) x (TY + 2S) per field and
-// plane, completion on an mbarrier per ring slot).  The plain kernel gives
-// each thread one output per plane; the z-blocked kernel gives each thread TZ
-// outputs along z and reuses every shared-memory read across them.  The shell
+// Data path: the padded fields are streamed plane by plane (z-marching) into a
+// shared-memory ring by TMA (cp.async.bulk.tensor, 2-D boxes of
+// (32 + 2S) x (TY + 2S) per plane, completion on an mbarrier per ring slot).
+// The plain kernel (FP64) reads the padded density n_b and the padded product
+// g_ab*n_b as two planes and gives each thread one output per plane.  The
+// z-blocked kernel (FP32) reads the interleaved pair (n_b, g_ab n_b) as one
+// 8-byte element per node, gives each thread TZ outputs along z, reuses every
+// shared-memory read across them, and sums both fields with packed f32x2
+// instructions.  The shell
 // offsets and unit vectors are compile-time immediates.  When Pout is given,
 // the kernels also store P = sum_e e^ n_b(r+e) of the pair ([3][N]), which the
 // discrete adjoint needs.
@@ -180,26 +183,50 @@ __host__ __device__ constexpr bool col_needs(unsigned mask, int k) {
     return false;
 }
 
-template <typename T, int S, int TZ, int TYB, int I>
-__device__ __forceinline__ void column_pair(const T *const *sb, T (*an)[3], T (*ag)[3]) {
-    using Tl = ShellTileZ<T, S, TZ, TYB>;
+// Packed pairs of FP32 values (x in the low half): the two sums of the shell force, over n_b and g_ab n_b,
+// run side by side as f32x2 instructions; each lane rounds like the scalar instruction.
+using f2 = unsigned long long;
+__device__ __forceinline__ f2 f2sub(f2 a, f2 b) {
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2add(f2 a, f2 b) {
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 f2fma(f2 a, f2 b, f2 c) {
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 f2splat(float u) {
+    f2 d;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(d) : "f"(u));
+    return d;
+}
+__device__ __forceinline__ float2 f2unpack(f2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+template <int S, int TZ, int TYB, int I>
+__device__ __forceinline__ void column_pair2(const f2 *const *sb, f2 (*acc)[3]) {
+    using Tl = ShellTileZ2<S, TZ, TYB>;
     constexpr int ex = ColTable<S>::cols.ex[I];
     constexpr int ey = ColTable<S>::cols.ey[I];
     constexpr unsigned mask = ColTable<S>::cols.mask[I];
     constexpr int offc = ey * Tl::BX + ex;
-    constexpr int GN = Tl::PLANE_BYTES / (int)sizeof(T);
     constexpr int NK = 2 * S + TZ;  // plane offsets k = -S .. S + TZ - 1
-    T cn[NK], cg[NK], mn[NK], mg[NK];
+    f2 cp[NK], cm[NK];
     [&]<int... K>(std::integer_sequence<int, K...>) {
         (
             [&] {
-                constexpr int k = K - S;
-                if constexpr (col_needs<S, TZ>(mask, k)) {
-                    const T *p = sb[K];
-                    cn[K] = p[offc];
-                    cg[K] = p[offc + GN];
-                    mn[K] = p[-offc];
-                    mg[K] = p[-offc + GN];
+                if constexpr (col_needs<S, TZ>(mask, K - S)) {
+                    cp[K] = sb[K][offc];
+                    cm[K] = sb[K][-offc];
                 }
             }(),
             ...);
@@ -211,48 +238,44 @@ __device__ __forceinline__ void column_pair(const T *const *sb, T (*an)[3], T (*
                 constexpr int ez = J % (2 * S + 1) - S;
                 if constexpr ((mask >> (ez + S)) & 1u) {
                     constexpr double len = ct_sqrt((double)(ex * ex + ey * ey + ez * ez));
-                    const T dn = cn[t + ez + S] - mn[t - ez + S];
-                    const T dg = cg[t + ez + S] - mg[t - ez + S];
-                    if constexpr (ex != 0) {
-                        constexpr T u = (T)(ex / len);
-                        an[t][0] += u * dn;
-                        ag[t][0] += u * dg;
-                    }
-                    if constexpr (ey != 0) {
-                        constexpr T u = (T)(ey / len);
-                        an[t][1] += u * dn;
-                        ag[t][1] += u * dg;
-                    }
-                    if constexpr (ez != 0) {
-                        constexpr T u = (T)(ez / len);
-                        an[t][2] += u * dn;
-                        ag[t][2] += u * dg;
-                    }
+                    const f2 d = f2sub(cp[t + ez + S], cm[t - ez + S]);
+                    if constexpr (ex != 0) acc[t][0] = f2fma(f2splat((float)(ex / len)), d, acc[t][0]);
+                    if constexpr (ey != 0) acc[t][1] = f2fma(f2splat((float)(ey / len)), d, acc[t][1]);
+                    if constexpr (ez != 0) acc[t][2] = f2fma(f2splat((float)(ez / len)), d, acc[t][2]);
                 }
             }(),
             ...);
     }(std::make_integer_sequence<int, TZ *(2 * S + 1)>{});
 }
 
-template <typename T, int S, int TZ, int TYB, int... I>
-__device__ __forceinline__ void all_columns(const T *const *sb, T (*an)[3], T (*ag)[3],
-                                            std::integer_sequence<int, I...>) {
-    (column_pair<T, S, TZ, TYB, I>(sb, an, ag), ...);
+template <int S, int TZ, int TYB, int... I>
+__device__ __forceinline__ void all_columns2(const f2 *const *sb, f2 (*acc)[3], std::integer_sequence<int, I...>) {
+    (column_pair2<S, TZ, TYB, I>(sb, acc), ...);
 }
 
-template <typename T, int S, int TZ, int TYB>
+// ---------------------------------------------------------------------------
+// z-blocked variant (FP32) on the interleaved field (n_b, g_ab n_b): each
+// thread produces TZ outputs along z.  The half shell is walked as column
+// pairs (ex, ey) / (-ex, -ey); every input pair of a column within the planes
+// t + D (t < TZ, D the column's z-offsets) is read from shared memory once
+// (one 8-byte load) and reused by all TZ outputs:
+//   d_t(ez) = a(x+ex, y+ey, z+t+ez) - a(x-ex, y-ey, z+t-ez),  ez in D,
+//   acc_t  += (ex, ey, ez)/|e| * d_t(ez),
+// both fields at once.  The centre column (0, 0, +-S) contributes only to the
+// z component.
+// ---------------------------------------------------------------------------
+template <int S, int TZ, int TYB>
 __global__ void __launch_bounds__(32 * TYB, 1)
-    k_shell_force_zb(const __grid_constant__ CUtensorMap map_n, const __grid_constant__ CUtensorMap map_gn, Grid g,
-                     int ox, const T *__restrict__ npad_a, const T *__restrict__ g_ab, T *__restrict__ Cout,
-                     T *__restrict__ Pout, T coef, int accumulate, int *err) {
-    using Tl = ShellTileZ<T, S, TZ, TYB>;
+    k_shell_force_zb(const __grid_constant__ CUtensorMap map_gn2, Grid g, int ox, const float *__restrict__ npad_a,
+                     const float *__restrict__ g_ab, float *__restrict__ Cout, float *__restrict__ Pout, float coef,
+                     int accumulate, int *err) {
+    using Tl = ShellTileZ2<S, TZ, TYB>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    T *ring = reinterpret_cast<T *>(base);
+    const f2 *ring = reinterpret_cast<const f2 *>(base);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
-    constexpr int SLOT = Tl::SLOT_BYTES / (int)sizeof(T);
-    constexpr int GN = Tl::PLANE_BYTES / (int)sizeof(T);
+    constexpr int SLOT = Tl::SLOT_BYTES / 8;
     constexpr int NK = 2 * S + TZ;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -263,22 +286,19 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     const bool leader = (tx == 0 && ty == 0);
     const int bx = x0 + g.H - S - ox;
     const int by = y0 + g.H - S;
-    constexpr uint32_t tx_bytes = 2u * Tl::PLANE * (uint32_t)sizeof(T);
+    constexpr uint32_t tx_bytes = (uint32_t)Tl::PLANE * 8u;
 
     if (leader) {
-        prefetch_tensormap(&map_n);
-        prefetch_tensormap(&map_gn);
+        prefetch_tensormap(&map_gn2);
         for (int r = 0; r < Tl::R; ++r) mbar_init(&bars[r], 1);
         fence_mbar_init();
     }
     __syncthreads();
     auto issue = [&](int j) {  // plane j holds interior z = z0 - S + j
         const int slot = j % Tl::R;
-        unsigned char *dst = base + slot * Tl::SLOT_BYTES;
         const int zp = z0 - S + j + g.H;
         mbar_arrive_expect_tx(&bars[slot], tx_bytes);
-        tma_load_3d(dst, &map_n, bx, by, zp, &bars[slot]);
-        tma_load_3d(dst + Tl::PLANE_BYTES, &map_gn, bx, by, zp, &bars[slot]);
+        tma_load_3d(base + slot * Tl::SLOT_BYTES, &map_gn2, bx, by, zp, &bars[slot]);
     };
     if (leader)
         for (int j = 0; j < Tl::R && j < nplanes; ++j) issue(j);
@@ -286,7 +306,7 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < g.nx) && (y < g.ny);
     const int toff = (ty + S) * Tl::BX + (tx + S + ox);
-    const T half = (T)0.5;
+    const float half = 0.5f;
 
     for (int s = 0; s < nsuper; ++s) {
         const int j0 = s * TZ;
@@ -294,7 +314,7 @@ __global__ void __launch_bounds__(32 * TYB, 1)
             if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
         if (active) {
             // the epilogue's global loads are issued before the shell sum so their latency hides behind it
-            T na[TZ], gr[TZ], old[TZ][3];
+            float na[TZ], gr[TZ], old[TZ][3];
             long long idx[TZ];
 #pragma unroll
             for (int t = 0; t < TZ; ++t) {
@@ -303,36 +323,29 @@ __global__ void __launch_bounds__(32 * TYB, 1)
                 na[t] = npad_a[pidx(g, x, y, z)];
                 gr[t] = g_ab[idx[t]];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) old[t][c] = accumulate ? Cout[(long long)c * g.N + idx[t]] : (T)0;
+                for (int c = 0; c < 3; ++c) old[t][c] = accumulate ? Cout[(long long)c * g.N + idx[t]] : 0.f;
             }
-            const T *sb[NK];
+            const f2 *sb[NK];
 #pragma unroll
             for (int k = 0; k < NK; ++k) sb[k] = ring + ((j0 + k) % Tl::R) * SLOT + toff;
-            T an[TZ][3], ag[TZ][3];
+            f2 acc[TZ][3];
 #pragma unroll
             for (int t = 0; t < TZ; ++t)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    an[t][c] = (T)0;
-                    ag[t][c] = (T)0;
-                }
+                for (int c = 0; c < 3; ++c) acc[t][c] = 0ull;
             // centre column (0, 0, +-S): e^ = (0, 0, 1) for ez = +S
 #pragma unroll
-            for (int t = 0; t < TZ; ++t) {
-                an[t][2] += sb[t + 2 * S][0] - sb[t][0];
-                ag[t][2] += sb[t + 2 * S][GN] - sb[t][GN];
-            }
-            all_columns<T, S, TZ, TYB>(sb, an, ag, std::make_integer_sequence<int, ColTable<S>::count>{});
+            for (int t = 0; t < TZ; ++t) acc[t][2] = f2add(acc[t][2], f2sub(sb[t + 2 * S][0], sb[t][0]));
+            all_columns2<S, TZ, TYB>(sb, acc, std::make_integer_sequence<int, ColTable<S>::count>{});
 #pragma unroll
             for (int t = 0; t < TZ; ++t) {
                 if (z0 + j0 + t < zend) {
-                    const T pre = coef * na[t];
+                    const float pre = coef * na[t];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        Cout[(long long)c * g.N + idx[t]] = old[t][c] + pre * (half * gr[t] * an[t][c] + half * ag[t][c]);
-                    if (Pout) {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) Pout[(long long)c * g.N + idx[t]] = an[t][c];
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 v = f2unpack(acc[t][c]);  // (sum over n_b, sum over g n_b)
+                        Cout[(long long)c * g.N + idx[t]] = old[t][c] + pre * (half * gr[t] * v.x + half * v.y);
+                        if (Pout) Pout[(long long)c * g.N + idx[t]] = v.x;
                     }
                 }
             }
@@ -345,12 +358,12 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     }
 }
 
-template <typename T, int S, int TZ, int TYB>
+template <int S, int TZ, int TYB>
 cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
-    using Tl = ShellTileZ<T, S, TZ, TYB>;
+    using Tl = ShellTileZ2<S, TZ, TYB>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_shell_force_zb<T, S, TZ, TYB>,
+        cudaError_t e = cudaFuncSetAttribute(k_shell_force_zb<S, TZ, TYB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Tl::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -359,9 +372,9 @@ cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
     dim3 block(Tl::TX, Tl::TY, 1);
     dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
     const int ox = ((g.H - S) % Tl::A + Tl::A) % Tl::A;
-    k_shell_force_zb<T, S, TZ, TYB><<<grid, block, Tl::SMEM, st>>>(*L.map_n, *L.map_gn, g, ox, (const T *)L.npad_a,
-                                                              (const T *)L.g_ab, (T *)L.Cout, (T *)L.Pout,
-                                                              (T)L.coef, L.accumulate, L.err);
+    k_shell_force_zb<S, TZ, TYB><<<grid, block, Tl::SMEM, st>>>(*L.map_gn, g, ox, (const float *)L.npad_a,
+                                                              (const float *)L.g_ab, (float *)L.Cout,
+                                                              (float *)L.Pout, (float)L.coef, L.accumulate, L.err);
     return cudaGetLastError();
 }
 
