@@ -3,8 +3,8 @@
 #include "lbe_adj_shell.cuh"
 
 namespace lbe {
-template cudaError_t launch_adj_tile<float, 1, 3, 16>(const AdjShellTile &, cudaStream_t);
-template cudaError_t launch_adj_tile<float, 2, 3, 16>(const AdjShellTile &, cudaStream_t);
-template cudaError_t launch_adj_tile<float, 3, 3, 16>(const AdjShellTile &, cudaStream_t);
-template cudaError_t launch_adj_tile<float, 4, 3, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<1, 3, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<2, 3, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<3, 3, 16>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<4, 3, 16>(const AdjShellTile &, cudaStream_t);
 }  // namespace lbe

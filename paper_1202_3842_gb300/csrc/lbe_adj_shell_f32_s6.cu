@@ -4,8 +4,8 @@
 #include "lbe_adj_shell.cuh"
 
 namespace lbe {
-extern template cudaError_t launch_adj_tile_cc<float, 6, 3, 16, 0>(const AdjShellTile &, cudaStream_t);
-extern template cudaError_t launch_adj_tile_cc<float, 6, 3, 16, 1>(const AdjShellTile &, cudaStream_t);
-extern template cudaError_t launch_adj_tile_cc<float, 6, 3, 16, 2>(const AdjShellTile &, cudaStream_t);
-template cudaError_t launch_adj_tile<float, 6, 3, 16>(const AdjShellTile &, cudaStream_t);
+extern template cudaError_t launch_adj_tile2_cc<6, 3, 16, 0>(const AdjShellTile &, cudaStream_t);
+extern template cudaError_t launch_adj_tile2_cc<6, 3, 16, 1>(const AdjShellTile &, cudaStream_t);
+extern template cudaError_t launch_adj_tile2_cc<6, 3, 16, 2>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<6, 3, 16>(const AdjShellTile &, cudaStream_t);
 }  // namespace lbe

@@ -2,5 +2,5 @@
 #include "lbe_adj_shell.cuh"
 
 namespace lbe {
-template cudaError_t launch_adj_tile_cc<float, 6, 3, 16, 1>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2_cc<6, 3, 16, 1>(const AdjShellTile &, cudaStream_t);
 }  // namespace lbe

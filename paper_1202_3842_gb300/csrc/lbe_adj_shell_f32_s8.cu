@@ -3,5 +3,5 @@
 #include "lbe_adj_shell.cuh"
 
 namespace lbe {
-template cudaError_t launch_adj_tile<float, 8, 1, 8>(const AdjShellTile &, cudaStream_t);
+template cudaError_t launch_adj_tile2<8, 1, 8>(const AdjShellTile &, cudaStream_t);
 }  // namespace lbe

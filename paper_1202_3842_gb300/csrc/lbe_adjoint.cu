@@ -300,8 +300,13 @@ __global__ void k_adj_shell_prep(Grid g, const T *__restrict__ npad_a, const T *
     for (int c = 0; c < 3; ++c) {
         const T lc = lC_a[(long long)c * g.N + i];
         const T L = s * lc;
-        write_padded<T>(g, Lpad + (long long)c * g.P, x, y, z, L);
-        write_padded<T>(g, gLpad + (long long)c * g.P, x, y, z, gv * L);
+        if constexpr (sizeof(T) == 4) {  // FP32: interleaved (Lambda_c, g Lambda_c), [3][P] float2 in Lpad
+            write_padded<float2>(g, reinterpret_cast<float2 *>(Lpad) + (long long)c * g.P, x, y, z,
+                                 make_float2(L, gv * L));
+        } else {
+            write_padded<T>(g, Lpad + (long long)c * g.P, x, y, z, L);
+            write_padded<T>(g, gLpad + (long long)c * g.P, x, y, z, gv * L);
+        }
         lp += L * P[(long long)c * g.N + i];
         cl += C_a[(long long)c * g.N + i] * lc;
     }
@@ -428,19 +433,22 @@ cudaError_t launch_adj_shell_prep(bool fp64, const Grid &g, const AdjShell &L, c
 
 template <typename T, int S, int TZ, int TYB>
 cudaError_t launch_adj_tile(const AdjShellTile &L, cudaStream_t st);
+template <int S, int TZ, int TYB>
+cudaError_t launch_adj_tile2(const AdjShellTile &L, cudaStream_t st);
 
-// Tile shapes equal those of the forward kernels, so the tensor-map boxes of shell_box() serve both.
+// FP32: interleaved (Lambda, g Lambda) tiles of the forward kernel (boxes of shell_box); FP64: two planes
+// (boxes of adj_shell_box).
 cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st) {
     if (!fp64) {
         switch (S) {
-            case 1: return launch_adj_tile<float, 1, 3, 16>(L, st);
-            case 2: return launch_adj_tile<float, 2, 3, 16>(L, st);
-            case 3: return launch_adj_tile<float, 3, 3, 16>(L, st);
-            case 4: return launch_adj_tile<float, 4, 3, 16>(L, st);
-            case 5: return launch_adj_tile<float, 5, 3, 16>(L, st);
-            case 6: return launch_adj_tile<float, 6, 3, 16>(L, st);
-            case 7: return launch_adj_tile<float, 7, 2, 16>(L, st);
-            case 8: return launch_adj_tile<float, 8, 1, 8>(L, st);
+            case 1: return launch_adj_tile2<1, 3, 16>(L, st);
+            case 2: return launch_adj_tile2<2, 3, 16>(L, st);
+            case 3: return launch_adj_tile2<3, 3, 16>(L, st);
+            case 4: return launch_adj_tile2<4, 3, 16>(L, st);
+            case 5: return launch_adj_tile2<5, 3, 16>(L, st);
+            case 6: return launch_adj_tile2<6, 3, 16>(L, st);
+            case 7: return launch_adj_tile2<7, 2, 16>(L, st);
+            case 8: return launch_adj_tile2<8, 1, 8>(L, st);
             default: return cudaErrorInvalidValue;
         }
     }

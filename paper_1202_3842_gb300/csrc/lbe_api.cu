@@ -1170,8 +1170,8 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     ATRY(alloc(lC, rb * M * 3 * N, true));
     ATRY(alloc(lF, rb * M * 3 * N, true));
     ATRY(alloc(lg, rb * M * M * N, true));
-    ATRY(alloc(Lpad, rb * 3 * P, true));
-    ATRY(alloc(gLpad, rb * 3 * P, true));
+    ATRY(alloc(Lpad, (f64 ? rb : 2 * rb) * 3 * P, true));  // FP32: interleaved (Lambda_c, g Lambda_c)
+    if (f64) ATRY(alloc(gLpad, rb * 3 * P, true));
     ATRY(alloc(lnbar, rb * M * P, true));
     ATRY(alloc(lmom, rb * M * 5 * N, false));
     ATRY(alloc(outA, 8 * N, false));
@@ -1188,10 +1188,16 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     std::vector<CUtensorMap> mapL(3 * npairs), mapgL(3 * npairs);
     for (int q = 0; q < npairs; ++q) {
         int bx = 0, by = 0;
-        adj_shell_box(f64, c->pairs[q].S, &bx, &by);
-        for (int cc = 0; cc < 3; ++cc) {
-            ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + rb * cc * P, bx, by));
-            ATRY(make_map(c, &mapgL[3 * q + cc], (char *)gLpad.p + rb * cc * P, bx, by));
+        if (f64) {
+            adj_shell_box(true, c->pairs[q].S, &bx, &by);
+            for (int cc = 0; cc < 3; ++cc) {
+                ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + rb * cc * P, bx, by));
+                ATRY(make_map(c, &mapgL[3 * q + cc], (char *)gLpad.p + rb * cc * P, bx, by));
+            }
+        } else {
+            shell_box(false, c->pairs[q].S, &bx, &by);
+            for (int cc = 0; cc < 3; ++cc)
+                ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + 2 * rb * cc * P, bx, by, true));
         }
     }
 

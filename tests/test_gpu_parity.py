@@ -305,3 +305,63 @@ def test_full_size_well256_sampled(prec):
     # a property that holds at any size: the mass is unchanged by the step
     m0 = arr["n"][0].sum()
     assert abs(n.sum() - m0) <= (1e-12 if prec == "fp64" else 1e-6) * m0
+
+
+def _subbox_channel(field, shape, centre, R, fill):
+    """Sub-box of a channel field: periodic along x, `fill` beyond the closed y and z axes."""
+    nx, ny, nz = shape
+    f = field.reshape(nz, ny, nx)
+    xs = [(centre[0] + d) % nx for d in range(-R, R + 1)]
+    out = np.full((2 * R + 1, 2 * R + 1, 2 * R + 1), fill, dtype=field.dtype)
+    for kz, z in enumerate(range(centre[2] - R, centre[2] + R + 1)):
+        if not 0 <= z < nz:
+            continue
+        for ky, y in enumerate(range(centre[1] - R, centre[1] + R + 1)):
+            if 0 <= y < ny:
+                out[kz, ky, :] = f[z, y, xs]
+    return out.reshape(-1)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_channel512_sampled(prec):
+    """The two-component bottleneck channel at its benchmark size and launch configuration: after one
+    step, n and J of both species at sampled nodes (bulk, near the walls, at the constriction's corners
+    and in its slit) equal the oracle's step of the sub-box around each sample.  Nodes beyond the closed
+    axes are solid in the sub-box (the walls already shield them; solid and outside both read as no
+    fluid).  One step of n and J depends on the initial state within 1 + 6 + 3 + 6 + 3 = 19 nodes."""
+    w = inputs.WORKLOADS["channel512"]()
+    arr = inputs.build_workload(w)
+    g = setup_gpu(w, arr, prec)
+    g.step(1)
+    n = np.stack([g.density(a) for a in range(2)])
+    J = np.stack([g.momentum(a) for a in range(2)])
+    shape = w["shape"]
+    R = 20
+    L = 2 * R + 1
+    # bulk; the slit's centre; fluid at the corners before, at the entry of, at the exit of and after the
+    # constriction; the slit next to a z wall; a y-z corner; the periodic x seam by a wall; one solid node
+    samples = [(100, 64, 64), (256, 64, 64), (223, 55, 64), (224, 56, 64), (287, 71, 30), (288, 72, 30),
+               (256, 57, 2), (5, 1, 126), (511, 126, 64), (230, 100, 100)]
+    tol_n = 1e-12 if prec == "fp64" else 1e-5
+    for (x, y, z) in samples:
+        o = oracle.Sim((L, L, L), (0, 0, 0), 2)
+        o.set_geometry(_subbox_channel(arr["solid"], shape, (x, y, z), R, 1))
+        for a in range(2):
+            o.set_species(a, w["sigma"][a], w["tau"][a])
+            o.set_body_force(a, w["body"][a])
+            o.init_density(a, _subbox_channel(arr["n"][a], shape, (x, y, z), R, 0.0))
+        o.step(1)
+        obs = o.observe()
+        c = R + L * (R + L * R)
+        i = x + shape[0] * (y + shape[1] * z)
+        for a in range(2):
+            nref = obs["n"][a][c]
+            assert abs(n[a, i] - nref) <= tol_n * max(nref, w["n0"][a]), (x, y, z, a, n[a, i], nref)
+            Jref = obs["J"][a][:, c]
+            Jscale = max(np.abs(Jref).max(), 1e-6 * CS * w["n0"][a])
+            assert np.abs(J[a, :, i] - Jref).max() <= (1e-12 if prec == "fp64" else 1e-3) * Jscale, (x, y, z, a)
+    # a property that holds at any size: the step conserves the mass of each species
+    for a in range(2):
+        m0 = arr["n"][a].sum()
+        assert abs(n[a].sum() - m0) <= (1e-12 if prec == "fp64" else 1e-6) * m0
+    g.close()
