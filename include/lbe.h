@@ -152,6 +152,13 @@ lbe_status lbe_get_density(lbe_ctx *ctx, int s, double *out);
  * barycentric u = sum J / sum n for s = -1; 0 where the density is 0. */
 lbe_status lbe_get_velocity(lbe_ctx *ctx, int s, double *out);
 
+/* Divergence of the velocity u^s (s = -1: the barycentric u) of the current
+ * state, out[N]: div u = (1/c_s^2) sum_p w_p c_p . u(r + c_p), the isotropic
+ * D3Q19 gradient, with u = 0 on solid nodes and outside closed axes.  The
+ * paper's compressibility check in the bottleneck (Sec. "Channel flow with a
+ * bottleneck": the steady flow should have div u = 0). */
+lbe_status lbe_get_divergence(lbe_ctx *ctx, int s, double *out);
+
 /* Momentum density J^s of the current state, out[3][N]. */
 lbe_status lbe_get_momentum(lbe_ctx *ctx, int s, double *out);
 

@@ -8,6 +8,8 @@
 //                         recovery transposed node by node; emits lambda_C, adds lambda_F
 //                         and the adjoint moments (ln, lPi, lJ) of each species;
 //         k_adj_write     the adjoint of the pre-collision populations from them
+//                         (three or four species; one or two species run all of K4^T
+//                         in k_adj_collide_pair, lbe_adj_collide_pair.cu)
 //   K3^T  k_adj_shell_prep / k_adj_shell_tile   shell force transposed: node-local
 //                         terms, then divergence-type shell sums of the weighted
 //                         adjoint from shared-memory tiles (lbe_adj_shell.cuh)
@@ -392,6 +394,9 @@ cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const ui
                                const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
                                const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF, void *lmom,
                                cudaStream_t st) {
+    if (ap.M <= 2)  // species-parallel lanes, all three passes in one kernel (lbe_adj_collide_pair.cu)
+        return launch_adj_collide_pair(p, g, post, mask, C, F, ap, lYf_in, lYg_in, lnd_in, lYf_out, lYg_out, lC, lF,
+                                       st);
     const unsigned nb = (unsigned)((g.N + ANT - 1) / ANT);
     const unsigned nbc = (unsigned)((g.N + ACT - 1) / ACT);
 #define LBE_ADJ_M(MM)                                                                                          \
@@ -400,8 +405,6 @@ cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const ui
                                                 (T *)lmom, (T *)lC, (T *)lF)
     LBE_ADJ_DISPATCH(p, {
         switch (ap.M) {
-            case 1: LBE_ADJ_M(1); break;
-            case 2: LBE_ADJ_M(2); break;
             case 3: LBE_ADJ_M(3); break;
             case 4: LBE_ADJ_M(4); break;
             default: return cudaErrorInvalidValue;

@@ -803,6 +803,20 @@ lbe_status lbe_get_velocity(lbe_ctx *c, int s, double *out) {
     return check_error_word(c);
 }
 
+lbe_status lbe_get_divergence(lbe_ctx *c, int s, double *out) {
+    TRY(ready(c));
+    if (s < -1 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
+    const long long N = c->g.N;
+    double *dn, *dJ;
+    TRY(state_moments(c, &dn, &dJ));
+    double *du = dJ + (long long)c->M * 3 * N;  // scratch holds n, J and 4 more fields
+    double *dd = du + 3 * N;
+    LAUNCH(launch_velocity(c->M, N, s, dn, dJ, du, nullptr, c->stream), "velocity kernel");
+    LAUNCH(launch_divergence(c->g, du, dd, c->stream), "divergence kernel");
+    CK(cudaMemcpyAsync(out, dd, 8 * N, cudaMemcpyDeviceToHost, c->stream), "copy divergence");
+    return check_error_word(c);
+}
+
 lbe_status lbe_get_force(lbe_ctx *c, int s, double *out) {
     TRY(ready(c));
     if (s < 0 || s >= c->M || !out) return fail(c, LBE_ERR_INVALID_ARG, "bad species index or null output");
@@ -1257,7 +1271,7 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                                       lYf[cl].p, lYg[cl].p, lnd[cl].p, lYf[1 - cl].p, lYg[1 - cl].p, lC.p, lF.p,
                                       lmom.p, c->stream),
                    "adjoint collide");
-            c->launches += 1;  // k_adj_collide + k_adj_write
+            if (M > 2) c->launches += 1;  // k_adj_collide + k_adj_write (one kernel for one or two species)
             CK(cudaMemsetAsync(lnd[1 - cl].p, 0, rb * M * N, c->stream), "memset");
             CK(cudaMemsetAsync(lg.p, 0, rb * M * M * N, c->stream), "memset");
             std::vector<int> own(M, 1);

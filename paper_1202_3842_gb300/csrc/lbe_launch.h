@@ -135,6 +135,8 @@ struct InvN0 {
 };
 cudaError_t launch_residual(int M, long long N, const InvN0 &inv, const double *n, double *rec, double *out,
                             cudaStream_t st);
+// div u [N] of a velocity field u [3][N] (FP64), isotropic D3Q19 gradient, u = 0 outside closed axes.
+cudaError_t launch_divergence(const Grid &g, const double *u, double *out, cudaStream_t st);
 // Convert a compute-precision field to FP64.
 cudaError_t launch_to_f64(bool fp64, const void *src, long long n, double *dst, cudaStream_t st);
 // Copy the interior of a padded field to a dense FP64 array.
@@ -182,6 +184,10 @@ cudaError_t launch_adj_collide(Prec p, const Grid &g, const void *post, const ui
                                const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
                                const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF,
                                void *lmom /* [M][5][N] scratch */, cudaStream_t st);
+cudaError_t launch_adj_collide_pair(Prec p, const Grid &g, const void *post, const uint32_t *mask, const void *C,
+                                   const void *F, const AdjParams &ap, const void *lYf_in, const void *lYg_in,
+                                   const void *lnd_in, void *lYf_out, void *lYg_out, void *lC, void *lF,
+                                   cudaStream_t st);
 cudaError_t launch_adj_shell_prep(bool fp64, const Grid &g, const AdjShell &L, cudaStream_t st);
 cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st);
 cudaError_t launch_adj_contact_prep(bool fp64, const Grid &g, const ContactParams &cp, const BallRows &br,

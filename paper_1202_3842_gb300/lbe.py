@@ -89,6 +89,7 @@ def lib():
             "lbe_save_state": [_P, _P, ctypes.POINTER(ctypes.c_size_t)],
             "lbe_load_state": [_P, _P, ctypes.c_size_t],
             "lbe_get_residual": [_P, _D],
+            "lbe_get_divergence": [_P, ctypes.c_int, _D],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -318,6 +319,12 @@ def lbe_get_residual(ctx):
     return v.value
 
 
+def lbe_get_divergence(ctx, N, s=-1):
+    out = np.empty(N)
+    _check(lib().lbe_get_divergence(ctx, int(s), _dp(out)), ctx)
+    return out
+
+
 def lbe_get_link_mask(ctx, N):
     out = np.empty(N, dtype=np.uint32)
     _check(lib().lbe_get_link_mask(ctx, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), ctx)
@@ -474,6 +481,10 @@ class Simulation:
 
     def load_state(self, state):
         lbe_load_state(self._h, state)
+
+    def divergence(self, s=-1):
+        """div u [N] of species s (-1: barycentric), isotropic D3Q19 gradient."""
+        return lbe_get_divergence(self._h, self.N, s)
 
     def residual(self):
         """max |n(t) - n(t0)| / ((t - t0) n0) since the previous call (-1 on the first call)."""

@@ -95,3 +95,48 @@ def test_residual_matches_oracle_densities():
         assert abs(got - expect) <= 1e-8 * expect, (got, expect)
         n_prev = n_now.copy()
     gpu.close()
+
+
+def _divergence(u, shape, periodic):
+    """div u = 3 sum_p w_p c_p . u(r + c_p), with u = 0 beyond closed axes (numpy, from the definition)."""
+    import oracle
+    c, w, _ = oracle.lattice()
+    nx, ny, nz = shape
+    U = u.reshape(3, nz, ny, nx)
+    out = np.zeros((nz, ny, nx))
+    for p in range(1, 19):
+        sh = [0, 0, 0]
+        for ax, (d, n, per) in enumerate(zip(c[p], shape, periodic)):
+            sh[ax] = int(d)
+        for comp in range(3):
+            if c[p][comp] == 0:
+                continue
+            v = U[comp]
+            # value at r + c_p: roll by -c_p along each axis, then zero what wrapped across a closed axis
+            r = np.roll(v, shift=(-sh[2], -sh[1], -sh[0]), axis=(0, 1, 2)).copy()
+            for ax, d, n, per in ((2, sh[0], nx, periodic[0]), (1, sh[1], ny, periodic[1]), (0, sh[2], nz, periodic[2])):
+                if per or d == 0:
+                    continue
+                idx = [slice(None)] * 3
+                idx[ax] = slice(n - 1, n) if d > 0 else slice(0, 1)
+                r[tuple(idx)] = 0.0
+            out += w[p] * c[p][comp] * r
+    return 3.0 * out.reshape(-1)
+
+
+def test_divergence_of_the_velocity_matches_oracle_fields():
+    from lbe_cases import setup_oracle
+    w, arr = _channel()
+    gsim = setup_gpu(w, arr, "fp64")
+    o = setup_oracle(w, arr)
+    gsim.step(25)
+    o.step(25)
+    obs = o.observe()
+    n, J = obs["n"].sum(0), obs["J"].sum(0)
+    u = np.where(n[None, :] > 0, J / np.where(n[None, :] > 0, n[None, :], 1.0), 0.0)
+    expect = _divergence(u, w["shape"], w["periodic"])
+    got = gsim.divergence(-1)
+    scale = np.abs(expect).max()
+    assert scale > 0
+    assert np.abs(got - expect).max() <= 1e-11 * scale
+    gsim.close()
