@@ -21,6 +21,8 @@
 // shared memory (an unrolled, predicated loop over the widest row: per-row
 // prefix sums and an exact-width switch were both measured slower).
 #pragma once
+#include <utility>
+
 #include "lbe_device.cuh"
 #include "lbe_launch.h"
 
@@ -41,11 +43,30 @@ struct ContactTile {
     static constexpr int LZ = 8;
 };
 
+// Ball sum of one species with a compile-time ball |d|^2 <= SQ/4 (SQ = sigma^2 of an integer diameter),
+// walked in the order of the runtime rows (dz, dy, dx ascending), so the sum is the same bit for bit.
+template <typename T, int RB, int BX, int SQ>
+__device__ __forceinline__ T ball_sum_ct(const T *const *sb, int boff) {
+    constexpr int W = 2 * RB + 1;
+    T acc = 0;
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+        (
+            [&] {
+                constexpr int dz = K / (W * W) - RB;
+                constexpr int dy = (K / W) % W - RB;
+                constexpr int dx = K % W - RB;
+                if constexpr (4 * (dx * dx + dy * dy + dz * dz) <= SQ) acc += sb[dz + RB][boff + dy * BX + dx];
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, W * W * W>{});
+    return acc;
+}
+
 struct ContactMaps {
     CUtensorMap m[MAXS];
 };
 
-template <typename T, int M, int RB, int MODE>
+template <typename T, int M, int RB, int MODE, int SQ0 = 0, int SQ1 = 0>
 __global__ void __launch_bounds__(256)
     k_contact_tma(const __grid_constant__ ContactMaps maps, Grid g, int ox, ContactParams cp, BallRows br,
                   T *__restrict__ gab, T *__restrict__ gnpad, T *__restrict__ xi_out,
@@ -107,16 +128,21 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int b = 0; b < M; ++b) {
                 T acc = 0;
+                if constexpr (SQ0 > 0) {  // balls known at compile time (common diameters): exact loads
+                    acc = b == 0 ? ball_sum_ct<T, RB, Tl::BX, SQ0>(sb, 0)
+                                 : ball_sum_ct<T, RB, Tl::BX, (SQ1 > 0 ? SQ1 : SQ0)>(sb, b * PL);
+                } else {
 #pragma unroll
-                for (int dz = -RB; dz <= RB; ++dz) {
-                    const T *pz = sb[dz + RB] + b * PL;
-                    const int k0 = br.first[b][dz + 4], k1 = br.first[b][dz + 5];
-                    for (int k = k0; k < k1; ++k) {
-                        const int a = br.a[b][k];
-                        const T *row = pz + br.dy[b][k] * Tl::BX;
+                    for (int dz = -RB; dz <= RB; ++dz) {
+                        const T *pz = sb[dz + RB] + b * PL;
+                        const int k0 = br.first[b][dz + 4], k1 = br.first[b][dz + 5];
+                        for (int k = k0; k < k1; ++k) {
+                            const int a = br.a[b][k];
+                            const T *row = pz + br.dy[b][k] * Tl::BX;
 #pragma unroll
-                        for (int dx = -RB; dx <= RB; ++dx)
-                            if (dx >= -a && dx <= a) acc += row[dx];
+                            for (int dx = -RB; dx <= RB; ++dx)
+                                if (dx >= -a && dx <= a) acc += row[dx];
+                        }
                     }
                 }
                 if constexpr (MODE == 1) {
@@ -161,12 +187,12 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-template <typename T, int M, int RB, int MODE>
+template <typename T, int M, int RB, int MODE, int SQ0 = 0, int SQ1 = 0>
 cudaError_t launch_ct(const ContactLaunch &L, cudaStream_t st) {
     using Tl = ContactTile<T, M, RB>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_contact_tma<T, M, RB, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(k_contact_tma<T, M, RB, MODE, SQ0, SQ1>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, Tl::SMEM);
         if (e != cudaSuccess) return e;
         attr = true;
@@ -177,13 +203,29 @@ cudaError_t launch_ct(const ContactLaunch &L, cudaStream_t st) {
     dim3 block(Tl::TX, Tl::TY, 1);
     dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
     const int ox = ((g.H - RB) % Tl::A + Tl::A) % Tl::A;
-    k_contact_tma<T, M, RB, MODE><<<grid, block, Tl::SMEM, st>>>(maps, g, ox, *L.cp, *L.br, (T *)L.gab,
+    k_contact_tma<T, M, RB, MODE, SQ0, SQ1><<<grid, block, Tl::SMEM, st>>>(maps, g, ox, *L.cp, *L.br, (T *)L.gab,
                                                                 (T *)L.gnpad, (T *)L.xi, L.mask, (T *)L.ln, L.err);
     return cudaGetLastError();
 }
 
+// sigma^2 of species b when sigma is an integer (0 otherwise)
+inline int sigma_sq(const ContactParams &cp, int b) {
+    const double s = cp.sigma[b];
+    const double r = (double)(long long)(s + 0.5);
+    return (s == r && r > 0.0 && r <= 8.0) ? (int)(r * r) : 0;
+}
+
 template <typename T, int M, int MODE>
 cudaError_t dispatch_rb(const ContactLaunch &L, cudaStream_t st) {
+    // compile-time balls for the common diameters: sigma 4/6 mixtures, sigma 6 and sigma 3
+    if constexpr (M == 2) {
+        if (L.RB == 3 && sigma_sq(*L.cp, 0) == 16 && sigma_sq(*L.cp, 1) == 36)
+            return launch_ct<T, 2, 3, MODE, 16, 36>(L, st);
+    }
+    if constexpr (M == 1) {
+        if (L.RB == 3 && sigma_sq(*L.cp, 0) == 36) return launch_ct<T, 1, 3, MODE, 36>(L, st);
+        if (L.RB == 1 && sigma_sq(*L.cp, 0) == 9) return launch_ct<T, 1, 1, MODE, 9>(L, st);
+    }
     switch (L.RB) {
         case 0: return launch_ct<T, M, 0, MODE>(L, st);
         case 1: return launch_ct<T, M, 1, MODE>(L, st);
