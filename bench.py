@@ -390,12 +390,9 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     except Exception as e:  # the state itself diverged (the timing is unaffected)
         umax = float("nan")
         state = "diverged: " + str(e)[:80]
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_step = ms / steps
-    value = world * N * M * steps / (ms * 1e-3) / 1e6
+    value = replica_value(world, N, M, steps, ms * 1e-3)
 
     dom = max(stages, key=lambda k: stages[k][0])
     dom_ms, dom_n = stages[dom]
@@ -485,6 +482,21 @@ def measure_adjoint(prec, wname="channel256adj", T=2000, K=100):
                     "amplitude and the body force"}
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over the ranks (replicas are timed together; the slowest one sets the job time)."""
+    if not dist:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(world, N, M, steps, seconds):
+    """Whole-job throughput of `world` independent lattices of N nodes and M species, in MLUPS per species."""
+    return world * N * M * steps / seconds / 1e6
+
+
 def run_ours(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -531,12 +543,8 @@ def run_ours(args):
         for a in range(M):
             lbe.lbe_get_density(sim._h, N, a, out.numpy())
         torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        result["e2e"] = {"value": world * N * M * args.steps / t_e2e / 1e6, "unit": "MLUPS/species",
+        t_e2e = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        result["e2e"] = {"value": replica_value(world, N, M, args.steps, t_e2e), "unit": "MLUPS/species",
                          "h2d_bytes_per_step": 8 * N * M / args.steps, "d2h_bytes_per_step": 8 * N * M / args.steps,
                          "what": "lbe_init_density from pinned host FP64 + %d x lbe_step + lbe_get_density to "
                                  "pinned host, wall clock" % args.steps}
