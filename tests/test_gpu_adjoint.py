@@ -55,6 +55,23 @@ def test_fp64_adjoint_matches_reference(consistent):
     np.testing.assert_array_equal(g1, g0)
 
 
+@pytest.mark.parametrize("sig,precs", [((1.0, 7.0), ("fp64", "fp32")), ((2.0, 8.0), ("fp32",))])
+def test_adjoint_every_shell_transpose_tile(sig, precs):
+    """The shell transpose of pair diameters 1, 4, 7 (FP64 and FP32 tiles) and 2, 5, 8 (FP32; FP64 stops at 7)
+    against the FP64 reference gradient: 1e-10 of the largest entry in FP64, 1e-3 in FP32."""
+    w, arr = _case(shape=(20, 18, 18), sig=sig, taus=(1.0, 0.9), width=8, length=6, seed=21)
+    T, axis, plane = 6, 0, 10
+    rPhi, rA, rG = _reference(w, arr, T, axis, plane)
+    for prec in precs:
+        g = setup_gpu(w, arr, prec)
+        Phi, dA, dG = g.adjoint_flux_gradient(T, 2, axis, plane)
+        tol = 1e-10 if prec == "fp64" else 1e-3
+        assert abs(Phi - rPhi) <= max(tol, 1e-12) * abs(rPhi), (prec, Phi, rPhi)
+        assert np.abs(dA - rA).max() <= tol * np.abs(rA).max(), prec
+        assert np.abs(dG - rG).max() <= tol * np.abs(rG).max(), prec
+        g.close()
+
+
 def _gpu_phi(w, arr, amp, gshift, T, axis, plane, prec="fp64"):
     a2 = dict(arr)
     a2["amp"] = amp

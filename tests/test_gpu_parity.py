@@ -94,6 +94,27 @@ def test_stage_parity_fp64(shape, sig):
         assert rel_err(C, obs["C"][a]) <= 1e-12
 
 
+@pytest.mark.parametrize("sig", [(1.0,), (2.0, 4.0), (4.0, 6.0), (6.0, 8.0), (8.0,), (3.0, 5.0)])
+def test_stage_parity_fp32_every_pair_diameter(sig):
+    """K1-K3 of one FP32 state against the oracle for pair diameters 1 to 8 (the FP32 shell tiles: three
+    outputs per thread along z up to 6, two at 7, one at 8) and both contact paths (compile-time balls for
+    sigma 4/6, runtime rows otherwise, up to ball radius 4).  Tolerance: 1e-5 of the largest value of each
+    field (FP32 sums over up to 762 shell points)."""
+    w, arr = case_channel((40, 22, 20), sig, 0.2, (1.0,) * len(sig), 10, 8)
+    rng = np.random.default_rng(9)
+    fl = arr["solid"] == 0
+    arr["n"] = arr["n"] * (1.0 + 0.2 * (rng.random(arr["n"].shape) - 0.5)) * fl[None, :]
+    g = setup_gpu(w, arr, "fp32")
+    o = setup_oracle(w, arr)
+    obs = o.observe()
+    M = len(sig)
+    for a in range(M):
+        assert rel_err(g.density(a), obs["n"][a]) <= 1e-6
+        for b in range(M):
+            assert rel_err(g.contact(a, b), obs["g"][a, b]) <= 1e-5
+        assert rel_err(g.force(a), obs["C"][a]) <= 1e-5
+
+
 # ---------------------------------------------------------------------------
 # FP64 dynamics
 # ---------------------------------------------------------------------------
