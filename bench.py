@@ -182,8 +182,8 @@ KERNEL_SOURCES = {
                 "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
     "shell": ["paper_1202_3842_gb300/csrc/lbe_shell.cu", "paper_1202_3842_gb300/csrc/lbe_shell.cuh",
               "paper_1202_3842_gb300/csrc/lbe_shell_kernels.cuh", "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
-    "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_device.cuh",
-                "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
+    "density": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu", "paper_1202_3842_gb300/csrc/lbe_collide_pair.cu",
+                "paper_1202_3842_gb300/csrc/lbe_device.cuh", "paper_1202_3842_gb300/csrc/lbe_node.cuh"],
     "contact": ["paper_1202_3842_gb300/csrc/lbe_contact.cu", "paper_1202_3842_gb300/csrc/lbe_contact.cuh",
                 "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "flux": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu"],

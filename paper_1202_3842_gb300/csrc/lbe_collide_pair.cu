@@ -10,7 +10,8 @@
 // population is two 64-byte runs, whole 32-byte sectors.  Compared with one
 // thread per node holding both species, the live state per thread halves,
 // which lets three CTAs of 256 threads share an SM.  One species: one thread
-// per node, 32 consecutive nodes per warp, u = J/n.
+// per node, 32 consecutive nodes per warp, u = J/n.  K1 (the pulled density)
+// uses the same lane layout.
 #include <math.h>
 
 #include <utility>
@@ -134,6 +135,34 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? 3 : 1)
     }(std::make_integer_sequence<int, Q>{});
 }
 
+// K1 for one or two species with the same lane layout: n^a(r) = sum_p f~_p(r) pulled, 0 on solid nodes,
+// into the padded stencil field with its periodic images (the arithmetic of k_density).
+template <typename S, typename T, int M, bool SOLID>
+__global__ void __launch_bounds__(NTP)
+    k_density_pair(Grid g, const S *__restrict__ pop, const uint32_t *__restrict__ mask, double n00, double n01,
+                   T *__restrict__ npad, int *err) {
+    static_assert(M == 1 || M == 2, "one or two species");
+    const int lane = threadIdx.x & 31;
+    const int a = M == 2 ? lane >> 4 : 0;
+    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x >> 5) * 16 + (lane & 15)
+                               : (long long)blockIdx.x * NTP + threadIdx.x;
+    if (i >= g.N) return;
+    int x, y, z;
+    node_xyz(g, i, x, y, z);
+    const uint32_t m = SOLID ? mask[i] : 0u;
+    T n = (T)0;
+    if (!(m & 1u)) {
+        const NbrOff o = nbr_offsets(g, x, y, z);
+        const S *fb = pop + pop_off(a, 0, 0, g.N);
+        const T n0 = (T)(a == 0 ? n00 : n01);
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+        }(std::make_integer_sequence<int, Q>{});
+        if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
+    }
+    write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);
+}
+
 #define LBE_PAIR_DISPATCH(p, ...)                                                      \
     switch (p) {                                                                       \
         case Prec::F64: { using S = double; using T = double; __VA_ARGS__; break; }    \
@@ -166,6 +195,32 @@ cudaError_t launch_collide_pair(Prec p, const Grid &g, const void *src, void *ds
         return cudaErrorInvalidValue;
     }
 #undef LBE_PAIR
+    return cudaGetLastError();
+}
+
+cudaError_t launch_density_pair(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
+                                const double *n0, void *npad, int *err, cudaStream_t st) {
+    const int per_cta = M == 2 ? NTP / 2 : NTP;
+    const unsigned nb = (unsigned)((g.N + per_cta - 1) / per_cta);
+    const double a0 = n0[0], a1 = M > 1 ? n0[1] : 0.0;
+#define LBE_DPAIR(MM, SOL) \
+    k_density_pair<S, T, MM, SOL><<<nb, NTP, 0, st>>>(g, (const S *)pop, mask, a0, a1, (T *)npad, err)
+    if (M == 1) {
+        if (solid) {
+            LBE_PAIR_DISPATCH(p, LBE_DPAIR(1, true));
+        } else {
+            LBE_PAIR_DISPATCH(p, LBE_DPAIR(1, false));
+        }
+    } else if (M == 2) {
+        if (solid) {
+            LBE_PAIR_DISPATCH(p, LBE_DPAIR(2, true));
+        } else {
+            LBE_PAIR_DISPATCH(p, LBE_DPAIR(2, false));
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+#undef LBE_DPAIR
     return cudaGetLastError();
 }
 

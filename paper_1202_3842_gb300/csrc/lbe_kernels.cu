@@ -228,6 +228,9 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
 
 cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
                            const double *n0, void *npad, int *err, cudaStream_t st) {
+    // one species: one thread per node at 32-42 registers (lbe_collide_pair.cu); measured faster than this
+    // kernel for one species (256^3 well 0.42 -> 0.31 ms) and slower for two (0.30 -> 0.32 ms)
+    if (M == 1) return launch_density_pair(p, g, pop, mask, solid, M, n0, npad, err, st);
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
     N0Vec n0v;
     for (int a = 0; a < MAXS; ++a) n0v.v[a] = a < M ? n0[a] : 0.0;

@@ -113,6 +113,9 @@ cudaError_t launch_collide_ablation(Prec p, const Grid &g, const void *src, void
                                     double *flux_buf, cudaStream_t st);
 cudaError_t launch_moments_ablation(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *C,
                                     const void *F, const StepParams &sp, double *n, double *J, cudaStream_t st);
+// K1 for one or two species, species-parallel lanes (lbe_collide_pair.cu).
+cudaError_t launch_density_pair(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
+                                const double *n0, void *npad, int *err, cudaStream_t st);
 // K4 for one or two species, species-parallel lanes (lbe_collide_pair.cu).
 cudaError_t launch_collide_pair(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                                 const void *C, const void *F, const StepParams &sp, double *flux_buf,
