@@ -240,8 +240,8 @@ lbe_status lbe_shell(double sigma, int *e, int cap, int *count);
  * Checkpoints every K = ckpt_every steps are kept and each segment is
  * recomputed in the reverse sweep, keeping the states of the segment and the
  * fields of their force stages (device memory: ceil(T/K) + K - 1 copies of the
- * populations, plus for each of the K steps M^2 + 3 M + 3 npairs words per
- * node and M (M + 1) words per node of the padded lattice).  FP64 and FP32 storage only
+ * populations, plus for each of the K steps M^2 + 3 M + 2 + 3 npairs words
+ * per node and M words per node of the padded lattice).  FP64 and FP32 storage only
  * (LBE_ERR_UNSUPPORTED for the 16-bit forms).  The state of the context is left as it was before the call;
  * the flux time average is reset.  Any output pointer may be NULL. */
 lbe_status lbe_adjoint_flux_gradient(lbe_ctx *ctx, int nsteps, int ckpt_every, int axis, int plane,
