@@ -39,6 +39,7 @@ sys.path.insert(0, ROOT)
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")  # JSON text
 FALLBACK_HBM_GBS = 6800.0
+FP64_NOMINAL_TFLOPS = 1.25
 SMS = 152
 FP32_LANES_PER_SM = 128
 QPOP = 19
@@ -73,6 +74,8 @@ def parse():
     p.add_argument("--adjoint-only", action="store_true", help="time only the adjoint against the forward")
     p.add_argument("--adjoint-steps", type=int, default=2000)
     p.add_argument("--adjoint-ckpt", type=int, default=100)
+    p.add_argument("--shell", default="auto", choices=["auto", "direct", "spectral"],
+                   help="K3 method: stencil sum, FFT convolution, or the library's choice")
     return p.parse_args()
 
 
@@ -304,10 +307,12 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
-def make_sim(w, arrays, prec):
+def make_sim(w, arrays, prec, shell="auto"):
     from paper_1202_3842_gb300 import lbe
     M = len(w["sigma"])
     sim = lbe.Simulation(w["shape"], w["periodic"], M, prec)
+    if shell != "auto":
+        sim.set_shell_method(shell)
     if arrays["solid"].any():
         sim.set_geometry(arrays["solid"])
     for a in range(M):
@@ -321,6 +326,19 @@ def make_sim(w, arrays, prec):
     if w["kind"] == "channel":
         sim.set_flux_plane(0, w["shape"][0] // 2)
     return sim
+
+
+def fft_size(n):
+    """Smallest m >= n whose prime factors are 2, 3, 5 and 7 (the library's choice of grid)."""
+    m = n
+    while True:
+        r = m
+        for p in (2, 3, 5, 7):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
 
 
 def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof):
@@ -355,7 +373,8 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     M = len(w["sigma"])
     nx, ny, nz = w["shape"]
     N = nx * ny * nz
-    sim = make_sim(w, arrays, prec)
+    sim = make_sim(w, arrays, prec, getattr(args, "shell", "auto"))
+    shell_method = sim.shell_method()
     sim.step(warmup)
     torch.cuda.synchronize()
     if sampler:
@@ -408,6 +427,35 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
                 "traffic": traffic_for("collide", wname, prec), "algorithmic_bytes_per_launch": alg,
                 "launches": dom_n, "avg_launch_ms": per_launch_ms,
                 "peak_source": peaks_kind + " hbm_gbs (STREAM-style copy)"}
+    elif shell_method == "spectral":
+        # M + M^2 real fields transformed forward and 3 M^2 + 3 M back per step.  FP64: bound by the FP64
+        # rate, counted as 2.5 L log2 L flops per real transform (half a complex transform of that size).
+        # FP32: bound by HBM, counted as one read and one write of every transformed field plus the
+        # pointwise kernels' fields, each touched once.
+        S_max = max(int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M))
+        L = [n if per else fft_size(n + S_max) for n, per in zip(w["shape"], w["periodic"])]
+        Lr = L[0] * L[1] * L[2]
+        Lc = (L[0] // 2 + 1) * L[1] * L[2]
+        nf, ni, nS = M + M * M, 3 * M * M + 3 * M, len(set(S for S in [
+            int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]))
+        common = {"kernel": "K3 spectral (cuFFT transforms + k_spec_embed/multiply/combine)", "traffic": None,
+                  "fft_grid": L, "launches": dom_n, "avg_launch_ms": per_launch_ms}
+        if prec == "fp64":
+            flops = (nf + ni) * 2.5 * Lr * math.log2(Lr)
+            achieved = flops / (per_launch_ms * 1e-3) / 1e12
+            roof = dict(common, bound="alu", achieved=achieved, peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
+                        frac=achieved / FP64_NOMINAL_TFLOPS, algorithmic_flops_per_launch=flops,
+                        peak_source="FP64 nominal vector rate of the part")
+        else:
+            rb = 4
+            byts = ((nf + ni) * (rb * Lr + 2 * rb * Lc)            # transforms: read + write once
+                    + nf * rb * Lr + (M + M * M) * rb * N            # embed
+                    + Lc * (2 * rb * nf + rb * 3 * nS + 2 * rb * ni)  # multiply
+                    + ni * rb * Lr + (M + M * M + 3 * M) * rb * N)   # combine
+            achieved = byts / (per_launch_ms * 1e-3) / 1e9
+            peak = float(peaks["hbm_gbs"])
+            roof = dict(common, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                        algorithmic_bytes_per_launch=byts, peak_source=peaks_kind + " hbm_gbs (STREAM-style copy)")
     else:
         S_list = [int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]
         flops = sum(shell_flops_per_node(S) for S in S_list) * N
@@ -426,7 +474,7 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     res = {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
            "mlups_nodes": value / M,
            "config": {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "nodes": N,
-                      "species": M,
+                      "species": M, "shell_method": shell_method,
                       "l2": "inputs larger than L2: population buffers %.2f GB each" % (N * M * 2 * QPOP * sb / 1e9),
                       "parallelism": "replicas only (one independent lattice per GPU)" if world > 1 else "1 GPU"},
            "roofline": roof,
@@ -532,7 +580,7 @@ def run_ours(args):
     if not args.no_e2e:
         pinned = [torch.from_numpy(arrays["n"][a].copy()).pin_memory() for a in range(M)]
         out = torch.empty(N, dtype=torch.float64).pin_memory()
-        sim = make_sim(w, arrays, args.prec)
+        sim = make_sim(w, arrays, args.prec, args.shell)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()

@@ -73,6 +73,24 @@ typedef enum {
  * (lbe_adjoint_flux_gradient) is that of LBE_DD_TR only. */
 typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_scheme;
 
+/* Method of the mean-field shell force C^{alpha,mf} (Appendix; the sums over
+ * the shell K_sigma of every species pair):
+ *   LBE_SHELL_DIRECT: the stencil sum, pair diameters 1..8 (FP32 and 16-bit
+ *     storage) or 1..7 (FP64);
+ *   LBE_SHELL_SPECTRAL: the same sums as circular convolutions by fast
+ *     Fourier transforms (cuFFT, loaded at run time) on a grid padded with
+ *     zeros along closed axes; any integer pair diameter up to the limit of
+ *     the contact values (sigma_b / 2 <= 4);
+ *   LBE_SHELL_AUTO (default): spectral for diameters without a compiled
+ *     stencil, and where it is cheaper by a cost rule measured on GB300: the
+ *     mean shell of the pairs above about 400 points (FP32 arithmetic) or 110
+ *     points (FP64, where the stencil is bound by the FP64 rate), scaled by
+ *     the padded grid over the lattice; direct otherwise.
+ * Both give the sums of the definition up to rounding.  The adjoint
+ * (lbe_adjoint_flux_gradient) needs every pair diameter to have a direct
+ * stencil. */
+typedef enum { LBE_SHELL_AUTO = 0, LBE_SHELL_DIRECT = 1, LBE_SHELL_SPECTRAL = 2 } lbe_shell_method;
+
 /* Optional device allocator.  alloc returns device memory of at least `bytes`
  * usable on `stream` (NULL on failure); free releases it.  NULL allocator:
  * the library uses cudaMallocAsync/cudaFreeAsync on the context stream. */
@@ -133,6 +151,15 @@ lbe_status lbe_set_wall_potential(lbe_ctx *ctx, const double *phi, const double 
 
 /* Uniform body force g[3] per unit mass on species s (Sec. "Channel flow"). */
 lbe_status lbe_set_body_force(lbe_ctx *ctx, int s, const double g[3]);
+
+/* Choose the method of the shell force (lbe_shell_method; takes effect at the
+ * next step).  LBE_ERR_INVALID_ARG for another value; LBE_ERR_UNSUPPORTED for
+ * LBE_SHELL_SPECTRAL when cuFFT cannot be loaded. */
+lbe_status lbe_set_shell_method(lbe_ctx *ctx, int method);
+
+/* The method the next step will use (LBE_SHELL_DIRECT or LBE_SHELL_SPECTRAL)
+ * for the species set so far; sets up the derived fields as a step would. */
+lbe_status lbe_get_shell_method(lbe_ctx *ctx, int *method);
 
 /* Populations at rest: f~_p = g~_p = w_p n[i] on fluid nodes, 0 on solid nodes
  * (so Pi(0) = n(0)).  n[N] >= 0.  Also sets the reference density n0 of the

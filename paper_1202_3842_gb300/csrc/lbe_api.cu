@@ -83,6 +83,15 @@ struct lbe_ctx {
     bool solid_links = false;  // some link can be blocked: a solid node or a closed axis
     int H = 0;
 
+    // K3 method (lbe_set_shell_method); the spectral method's cuFFT plans and buffers
+    int shell_method = LBE_SHELL_AUTO;
+    bool spectral = false;
+    SpectralShell *spec = nullptr;
+    int specL[3] = {0, 0, 0};
+    long long specNr = 0, specNc = 0;
+    SpecPairs specPairs{};
+    Buf specR, specZ, specW, specTab, specWork;
+
     long long steps = 0;
     long long flux_count = 0;
     int flux_axis = -1, flux_plane = -1;
@@ -271,6 +280,166 @@ bool integer_diameter(double s, int *S) {
     return true;
 }
 
+// Smallest n' >= n whose prime factors are 2, 3, 5 and 7 (sizes cuFFT transforms well).
+int fft_size(int n) {
+    for (int m = n;; ++m) {
+        int r = m;
+        for (int p : {2, 3, 5, 7})
+            while (r % p == 0) r /= p;
+        if (r == 1) return m;
+    }
+}
+
+// The row kernels of the spectral form take y and z from the grid's second and third dimensions.
+bool spectral_shape_ok(const lbe_ctx *c, int Smax) {
+    const Grid &g = c->g;
+    const int ly = g.per[1] ? g.ny : fft_size(g.ny + Smax), lz = g.per[2] ? g.nz : fft_size(g.nz + Smax);
+    return ly <= 65535 && lz <= 65535;
+}
+
+int shell_count(int S) {
+    int k = 0;
+    for (int z = -S; z <= S; ++z)
+        for (int y = -S; y <= S; ++y)
+            for (int x = -S; x <= S; ++x)
+                if (in_shell(S, x, y, z)) ++k;
+    return k;
+}
+
+// Cost rule of LBE_SHELL_AUTO, from measurements on GB300 (512x128x128 two-species channel, pair
+// diameters 4, 5, 5, 6; 256^3 one-species well, diameter 6): the stencil costs a fixed time per node
+// and shell point, the spectral form a fixed time per grid point and pair (its transforms and
+// pointwise kernels), and the two break even at a mean shell of about 400 points per pair in FP32
+// (both workloads: 395 and 403) and about 110 in FP64, where the stencil is bound by the FP64 rate.
+bool spectral_cheaper(const lbe_ctx *c, bool f64) {
+    long long pts = 0;
+    int Smax = 0;
+    for (const auto &ps : c->pairs) {
+        pts += shell_count(ps.S);
+        Smax = std::max(Smax, ps.S);
+    }
+    const Grid &g = c->g;
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    double Nr = 1.0;
+    for (int k = 0; k < 3; ++k) Nr *= g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
+    const double even = f64 ? 110.0 : 400.0;
+    return spectral_shape_ok(c, Smax) && (double)pts * (double)g.N > even * (double)c->pairs.size() * Nr;
+}
+
+// Plans, buffers and shell spectra of the spectral K3 (lbe_spectral.cu) for the current pairs.
+lbe_status spectral_setup(lbe_ctx *c) {
+    const bool f64 = prec_fp64(c->prec);
+    const size_t rb = real_bytes(c);
+    const Grid &g = c->g;
+    int Smax = 0;
+    std::vector<int> shells;
+    SpecPairs sp{};
+    sp.M = c->M;
+    sp.npairs = (int)c->pairs.size();
+    for (int q = 0; q < sp.npairs; ++q) {
+        const PairShell &ps = c->pairs[q];
+        Smax = std::max(Smax, ps.S);
+        int s = 0;
+        while (s < (int)shells.size() && shells[s] != ps.S) ++s;
+        if (s == (int)shells.size()) shells.push_back(ps.S);
+        sp.a[q] = ps.a;
+        sp.b[q] = ps.b;
+        sp.s[q] = s;
+        sp.half_coef[q] = 0.5 * ps.coef;
+    }
+    // the grid: the lattice along periodic axes; at least Smax zero planes beyond it along closed axes
+    const int n3[3] = {g.nx, g.ny, g.nz};
+    int L[3];
+    for (int k = 0; k < 3; ++k) L[k] = g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
+    if (!spectral_shape_ok(c, Smax))
+        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: an axis of the grid is longer than 65535");
+    const int nfwd = c->M + sp.npairs, ninv = 3 * sp.npairs + 3 * c->M, nS = (int)shells.size();
+    spectral_destroy(c->spec);
+    c->spec = nullptr;
+    std::string why;
+    size_t ws = 0;
+    if (spectral_create(&c->spec, f64, L, nfwd, ninv, &ws, &why) != 0)
+        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: " + why);
+    const long long Nr = (long long)L[0] * L[1] * L[2], Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
+    TRY(dev_alloc(c, c->specR, rb * (size_t)std::max(ninv, std::max(nfwd, 3)) * Nr));
+    TRY(dev_alloc(c, c->specZ, 2 * rb * (size_t)std::max(nfwd, 3) * Nc));
+    TRY(dev_alloc(c, c->specW, 2 * rb * (size_t)ninv * Nc));
+    TRY(dev_alloc(c, c->specTab, rb * 3 * (size_t)nS * Nc));
+    TRY(dev_alloc(c, c->specWork, ws));
+    if (spectral_bind(c->spec, c->specWork.p, c->stream) != 0)
+        return fail(c, LBE_ERR_CUDA, "spectral shell force: binding the cuFFT work area failed");
+    for (int k = 0; k < 3; ++k) c->specL[k] = L[k];
+    c->specNr = Nr;
+    c->specNc = Nc;
+    c->specPairs = sp;
+    // shell spectra t_c = Im FFT(kappa_c), kappa_c(-e mod L) = e_c / |e|
+    std::vector<std::vector<int>> eh(nS);
+    std::vector<std::vector<double>> uh(nS);
+    std::vector<Buf> ed(nS), ud(nS);
+    lbe_status st = LBE_OK;
+    for (int s = 0; s < nS && st == LBE_OK; ++s) {
+        const int S = shells[s];
+        for (int z = -S; z <= S; ++z)
+            for (int y = -S; y <= S; ++y)
+                for (int x = -S; x <= S; ++x)
+                    if (in_shell(S, x, y, z)) {
+                        const double len = std::sqrt((double)(x * x + y * y + z * z));
+                        eh[s].insert(eh[s].end(), {x, y, z});
+                        uh[s].insert(uh[s].end(), {x / len, y / len, z / len});
+                    }
+        const int ne = (int)(eh[s].size() / 3);
+        if ((st = dev_alloc(c, ed[s], sizeof(int) * eh[s].size())) != LBE_OK) break;
+        if ((st = dev_alloc(c, ud[s], sizeof(double) * uh[s].size())) != LBE_OK) break;
+        cudaError_t e = cudaMemcpyAsync(ed[s].p, eh[s].data(), sizeof(int) * eh[s].size(), cudaMemcpyHostToDevice,
+                                        c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ud[s].p, uh[s].data(), sizeof(double) * uh[s].size(), cudaMemcpyHostToDevice,
+                                c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->specR.p, 0, rb * 3 * Nr, c->stream);
+        if (e == cudaSuccess)
+            e = launch_spec_table(f64, c->specR.p, Nr, L, (const int *)ed[s].p, (const double *)ud[s].p, ne, c->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "spectral shell tables");
+            break;
+        }
+        c->launches += 1;
+        if (spectral_forward(c->spec, 2, c->specR.p, c->specZ.p) != 0) {
+            st = fail(c, LBE_ERR_CUDA, "spectral shell tables: cuFFT forward transform failed");
+            break;
+        }
+        e = launch_spec_imag(f64, c->specZ.p, (char *)c->specTab.p + rb * 3 * (size_t)s * Nc, Nc, c->stream);
+        c->launches += 1;
+        if (e != cudaSuccess) st = cuda_fail(c, e, "spectral shell tables");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);  // the host lists must outlive their copies
+    for (int s = 0; s < nS; ++s) {
+        dev_free(c, ed[s]);
+        dev_free(c, ud[s]);
+    }
+    if (st != LBE_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(c, e, "spectral shell tables");
+    return LBE_OK;
+}
+
+// K3 in spectral form for every pair: C [M][3][N] (and P [npairs][3][N] into Pbase for the adjoint).
+lbe_status spectral_shell(lbe_ctx *c, void *Pbase) {
+    const bool f64 = prec_fp64(c->prec);
+    LAUNCH(launch_spec_embed(f64, c->g, c->specL, c->specNr, c->npad.p, c->gab.p, c->specPairs, c->specR.p,
+                             c->stream),
+           "spectral embed");
+    if (spectral_forward(c->spec, 0, c->specR.p, c->specZ.p) != 0)
+        return fail(c, LBE_ERR_CUDA, "spectral shell force: cuFFT forward transform failed");
+    LAUNCH(launch_spec_multiply(f64, c->specZ.p, c->specTab.p, c->specW.p, c->specNc, c->specPairs,
+                                1.0 / (double)c->specNr, c->stream),
+           "spectral multiply");
+    if (spectral_inverse(c->spec, c->specW.p, c->specR.p) != 0)
+        return fail(c, LBE_ERR_CUDA, "spectral shell force: cuFFT inverse transform failed");
+    LAUNCH(launch_spec_combine(f64, c->g, c->specL, c->specNr, c->specR.p, c->npad.p, c->gab.p, c->specPairs,
+                               c->C.p, Pbase, c->stream),
+           "spectral combine");
+    return LBE_OK;
+}
+
 // Set up everything that depends on the species, geometry and potentials:
 // halo width, padded fields, tensor maps, ball tables, force field.
 lbe_status prepare(lbe_ctx *c) {
@@ -281,14 +450,16 @@ lbe_status prepare(lbe_ctx *c) {
         // pair shells
         c->pairs.clear();
         int H = 1;
+        bool direct_ok = true;  // every pair diameter has a compiled direct stencil
         for (int a = 0; a < c->M; ++a)
             for (int b = 0; b < c->M; ++b) {
                 double sab = 0.5 * (c->sigma[a] + c->sigma[b]);
                 if (!(sab > 0.0)) continue;
                 int S = 0;
-                if (!integer_diameter(sab, &S) || !shell_supported(f64, S))
+                if (!integer_diameter(sab, &S) || S > 16)
                     return fail(c, LBE_ERR_UNSUPPORTED,
-                                "pair diameter " + std::to_string(sab) + " has no compiled shell stencil");
+                                "pair diameter " + std::to_string(sab) + " is not an integer of at most 16");
+                if (!shell_supported(f64, S)) direct_ok = false;
                 PairShell ps{};
                 ps.a = a;
                 ps.b = b;
@@ -297,6 +468,16 @@ lbe_status prepare(lbe_ctx *c) {
                 c->pairs.push_back(ps);
                 H = std::max(H, S);
             }
+        // K3 method: the direct stencil, or the spectral form for FP64 (bound by the FP64 rate) and
+        // for diameters without a compiled stencil
+        c->spectral = false;
+        if (!c->pairs.empty()) {
+            if (c->shell_method == LBE_SHELL_DIRECT && !direct_ok)
+                return fail(c, LBE_ERR_UNSUPPORTED,
+                            "a pair diameter has no compiled direct shell stencil (the spectral method takes it)");
+            c->spectral = c->shell_method == LBE_SHELL_SPECTRAL ||
+                          (c->shell_method == LBE_SHELL_AUTO && (!direct_ok || spectral_cheaper(c, f64)));
+        }
         // ball radii
         ContactParams cp{};
         cp.M = c->M;
@@ -360,6 +541,7 @@ lbe_status prepare(lbe_ctx *c) {
         CK(cudaMemsetAsync(c->gnpad.p, 0, gnb, c->stream), "memset gnpad");
         CK(cudaMemsetAsync(c->C.p, 0, rb * c->M * 3 * g.N, c->stream), "memset C");
         for (auto &ps : c->pairs) {
+            if (!shell_supported(f64, ps.S)) continue;  // spectral only
             char *nb = (char *)c->npad.p + rb * ps.b * g.P;
             char *gn = (char *)c->gnpad.p + (f64 ? rb : 2 * rb) * (ps.a * c->M + ps.b) * g.P;
             int bx = 0, by = 0;
@@ -373,6 +555,7 @@ lbe_status prepare(lbe_ctx *c) {
             for (int b = 0; b < c->M; ++b)
                 TRY(make_map(c, &c->contact_maps[b], (char *)c->npad.p + rb * b * g.P, bx, by));
         }
+        if (c->spectral) TRY(spectral_setup(c));
         c->fields_dirty = false;
     }
     if (c->force_dirty) {
@@ -434,6 +617,10 @@ lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = null
         L.xi = xibase;
         L.err = (int *)c->err.p;
         LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
+    }
+    if (c->spectral) {
+        StageTimer t(c, LBE_STAGE_SHELL);
+        return spectral_shell(c, Pbase);
     }
     std::vector<int> first(c->M, 1);
     for (size_t q = 0; q < c->pairs.size(); ++q) {
@@ -651,10 +838,34 @@ void lbe_destroy(lbe_ctx *c) {
     c->ev_pool.clear();
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
-                  &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec};
+                  &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec,
+                  &c->specR, &c->specZ, &c->specW, &c->specTab, &c->specWork};
+    spectral_destroy(c->spec);
+    c->spec = nullptr;
     for (Buf *b : all) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     delete c;
+}
+
+lbe_status lbe_set_shell_method(lbe_ctx *c, int method) {
+    TRY(ready(c));
+    if (method < LBE_SHELL_AUTO || method > LBE_SHELL_SPECTRAL)
+        return fail(c, LBE_ERR_INVALID_ARG, "shell method must be LBE_SHELL_AUTO, _DIRECT or _SPECTRAL");
+    if (method == LBE_SHELL_SPECTRAL) {
+        std::string why;
+        if (!spectral_available(&why)) return fail(c, LBE_ERR_UNSUPPORTED, why);
+    }
+    c->shell_method = method;
+    c->fields_dirty = true;
+    return LBE_OK;
+}
+
+lbe_status lbe_get_shell_method(lbe_ctx *c, int *method) {
+    TRY(ready(c));
+    if (!method) return fail(c, LBE_ERR_INVALID_ARG, "null method");
+    TRY(prepare(c));
+    *method = c->spectral ? LBE_SHELL_SPECTRAL : LBE_SHELL_DIRECT;
+    return LBE_OK;
 }
 
 lbe_status lbe_set_geometry(lbe_ctx *c, const uint8_t *solid) {
@@ -1132,6 +1343,10 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     if (c->cfg.scheme != LBE_DD_TR) return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint is that of the DD-TR scheme");
     TRY(prepare(c));
     const bool f64 = prec_fp64(c->prec);
+    for (const auto &ps : c->pairs)
+        if (!shell_supported(f64, ps.S))
+            return fail(c, LBE_ERR_UNSUPPORTED, "the shell transpose has no compiled stencil for pair diameter " +
+                                                    std::to_string(ps.S));
     const size_t rb = real_bytes(c);
     const long long N = c->g.N, P = c->g.P;
     const int M = c->M;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lbe_device.cuh"
 
 namespace lbe {
@@ -197,5 +199,33 @@ cudaError_t launch_adj_contact_prep(bool fp64, const Grid &g, const ContactParam
                                    const void *xi, const void *lg, void *lnbar, cudaStream_t st);
 cudaError_t launch_adj_amp(bool fp64, const Grid &g, int M, const void *lF, const double *phi, double *out,
                            cudaStream_t st);
+
+// K3 by fast Fourier transforms (lbe_spectral.cu).
+struct SpecPairs {
+    int M, npairs;
+    int a[MAXS * MAXS], b[MAXS * MAXS];  // species of each ordered pair
+    int s[MAXS * MAXS];                  // index of the pair's shell spectrum
+    double half_coef[MAXS * MAXS];       // coef_ab / 2
+};
+struct SpectralShell;  // cuFFT plans of one lattice
+bool spectral_available(std::string *why);
+// Plans for the grid L (x fastest): forward of nfwd real fields, inverse of ninv half spectra, and a
+// three-field forward for the shell tables.  Returns 0, or -1 with the reason in *why.
+int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, int ninv, size_t *work_bytes,
+                    std::string *why);
+void spectral_destroy(SpectralShell *s);
+int spectral_bind(SpectralShell *s, void *work, cudaStream_t st);
+int spectral_forward(SpectralShell *s, int which /* 0: nfwd fields, 2: three table fields */, void *R, void *Z);
+int spectral_inverse(SpectralShell *s, void *W, void *R);
+cudaError_t launch_spec_table(bool fp64, void *R3, long long Nr, const int L[3], const int *e, const double *u, int ne,
+                              cudaStream_t st);
+cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc, cudaStream_t st);
+cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const void *npad,
+                              const void *gab, const SpecPairs &sp, void *R, cudaStream_t st);
+cudaError_t launch_spec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc, const SpecPairs &sp,
+                                 double scale, cudaStream_t st);
+cudaError_t launch_spec_combine(bool fp64, const Grid &g, const int L[3], long long Nr, const void *R,
+                                const void *npad, const void *gab, const SpecPairs &sp, void *Cout, void *Pout,
+                                cudaStream_t st);
 
 }  // namespace lbe

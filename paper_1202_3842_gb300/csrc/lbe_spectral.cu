@@ -1,0 +1,345 @@
+// K3 by fast Fourier transforms: the spectral form of the mean-field shell force.
+//
+// The shell sums of one ordered pair (a, b) (Appendix, hard-sphere C^{alpha,mf})
+//   P(r) = sum_{e in K_S} e^ n_b(r + e),   Q(r) = sum_{e in K_S} e^ (g_ab n_b)(r + e),
+// are correlations of the densities with the fixed odd kernel K_S(e) = e / |e|.  On a grid that
+// equals the lattice along periodic axes and carries at least S zero planes beyond the lattice along
+// closed axes (the zero ghosts of a closed axis), a correlation is a circular convolution with
+// kappa(x) = K_S(-x mod L), so
+//   P^(k) = kappa^(k) n^(k),   kappa^(k) = i t(k),
+// t real because kappa is real and odd.  The three components of t are tabulated once per shell by
+// transforming kappa itself.  One force stage then runs
+//   1. k_spec_embed: n_b and g_ab n_b of every pair into the zero-padded grid;
+//   2. one batched forward transform of those M + pairs fields;
+//   3. k_spec_multiply: the P spectra of every pair and component, and per species the Q spectra
+//      summed with coef_ab / 2 (the inverse transform is linear), scaled by 1 / (L0 L1 L2);
+//   4. one batched inverse transform of the 3 pairs + 3 M spectra;
+//   5. k_spec_combine: C^a(r) = n_a(r) [ sum_b coef_ab / 2 g_ab(r) P_ab(r) + Qsum_a(r) ], the
+//      arithmetic of the direct kernel regrouped (and P itself when the adjoint keeps it).
+// The transforms are cuFFT's (a library FFT, like a library GEMM), loaded at run time from
+// libcufft.so.12 so that the library still needs only libcuda to load; without it the spectral
+// method reports LBE_ERR_UNSUPPORTED.
+#include <cufft.h>
+#include <dlfcn.h>
+
+#include <mutex>
+#include <type_traits>
+#include <string>
+
+#include "lbe_device.cuh"
+#include "lbe_launch.h"
+
+namespace lbe {
+
+namespace {
+
+struct CufftApi {
+    decltype(&cufftCreate) create;
+    decltype(&cufftDestroy) destroy;
+    decltype(&cufftSetAutoAllocation) set_auto;
+    decltype(&cufftMakePlanMany) make_many;
+    decltype(&cufftSetWorkArea) set_work;
+    decltype(&cufftSetStream) set_stream;
+    decltype(&cufftExecR2C) r2c;
+    decltype(&cufftExecC2R) c2r;
+    decltype(&cufftExecD2Z) d2z;
+    decltype(&cufftExecZ2D) z2d;
+};
+
+const CufftApi *cufft_api(std::string *why) {
+    static std::mutex mu;
+    static int state = 0;  // 0: not tried, 1: loaded, -1: missing
+    static CufftApi api{};
+    static std::string reason;
+    std::lock_guard<std::mutex> lock(mu);
+    if (state == 0) {
+        void *h = nullptr;
+        for (const char *name : {"libcufft.so.12", "libcufft.so", "/usr/local/cuda/lib64/libcufft.so.12"}) {
+            h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+            if (h) break;
+        }
+        if (!h) {
+            state = -1;
+            reason = "cuFFT (libcufft.so.12) could not be loaded";
+        } else {
+            bool ok = true;
+            auto get = [&](auto &fp, const char *sym) {
+                fp = reinterpret_cast<std::remove_reference_t<decltype(fp)>>(dlsym(h, sym));
+                if (!fp) ok = false;
+            };
+            get(api.create, "cufftCreate");
+            get(api.destroy, "cufftDestroy");
+            get(api.set_auto, "cufftSetAutoAllocation");
+            get(api.make_many, "cufftMakePlanMany");
+            get(api.set_work, "cufftSetWorkArea");
+            get(api.set_stream, "cufftSetStream");
+            get(api.r2c, "cufftExecR2C");
+            get(api.c2r, "cufftExecC2R");
+            get(api.d2z, "cufftExecD2Z");
+            get(api.z2d, "cufftExecZ2D");
+            state = ok ? 1 : -1;
+            if (!ok) reason = "libcufft.so.12 lacks a needed entry point";
+        }
+    }
+    if (state < 0) {
+        if (why) *why = reason;
+        return nullptr;
+    }
+    return &api;
+}
+
+}  // namespace
+
+struct SpectralShell {
+    const CufftApi *api = nullptr;
+    bool fp64 = false;
+    int L[3] = {0, 0, 0};
+    long long Nr = 0, Nc = 0;
+    cufftHandle plan[3] = {0, 0, 0};  // forward (nfwd fields), inverse (ninv), table (3 fields)
+    bool made[3] = {false, false, false};
+};
+
+bool spectral_available(std::string *why) { return cufft_api(why) != nullptr; }
+
+void spectral_destroy(SpectralShell *s) {
+    if (!s) return;
+    for (int k = 0; k < 3; ++k)
+        if (s->made[k]) s->api->destroy(s->plan[k]);
+    delete s;
+}
+
+int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, int ninv, size_t *work_bytes,
+                    std::string *why) {
+    *out = nullptr;
+    const CufftApi *api = cufft_api(why);
+    if (!api) return -1;
+    SpectralShell *s = new SpectralShell();
+    s->api = api;
+    s->fp64 = fp64;
+    for (int k = 0; k < 3; ++k) s->L[k] = L[k];
+    s->Nr = (long long)L[0] * L[1] * L[2];
+    s->Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
+    int n[3] = {L[2], L[1], L[0]};  // row-major: x is the fastest (and the halved) dimension
+    const int batch[3] = {nfwd, ninv, 3};
+    const cufftType type[3] = {fp64 ? CUFFT_D2Z : CUFFT_R2C, fp64 ? CUFFT_Z2D : CUFFT_C2R,
+                               fp64 ? CUFFT_D2Z : CUFFT_R2C};
+    size_t wmax = 0;
+    for (int k = 0; k < 3; ++k) {
+        cufftResult r = api->create(&s->plan[k]);
+        if (r != CUFFT_SUCCESS) {
+            if (why) *why = "cufftCreate failed (" + std::to_string((int)r) + ")";
+            spectral_destroy(s);
+            return -1;
+        }
+        s->made[k] = true;
+        api->set_auto(s->plan[k], 0);
+        size_t ws = 0;
+        r = api->make_many(s->plan[k], 3, n, nullptr, 1, 0, nullptr, 1, 0, type[k], batch[k], &ws);
+        if (r != CUFFT_SUCCESS) {
+            if (why) *why = "cufftMakePlanMany failed (" + std::to_string((int)r) + ")";
+            spectral_destroy(s);
+            return -1;
+        }
+        wmax = ws > wmax ? ws : wmax;
+    }
+    *work_bytes = wmax;
+    *out = s;
+    return 0;
+}
+
+int spectral_bind(SpectralShell *s, void *work, cudaStream_t st) {
+    for (int k = 0; k < 3; ++k) {
+        if (s->api->set_work(s->plan[k], work) != CUFFT_SUCCESS) return -1;
+        if (s->api->set_stream(s->plan[k], st) != CUFFT_SUCCESS) return -1;
+    }
+    return 0;
+}
+
+// which: 0 forward (nfwd fields), 2 table (3 fields); real -> half spectrum
+int spectral_forward(SpectralShell *s, int which, void *R, void *Z) {
+    cufftResult r = s->fp64 ? s->api->d2z(s->plan[which], (double *)R, (cufftDoubleComplex *)Z)
+                            : s->api->r2c(s->plan[which], (float *)R, (cufftComplex *)Z);
+    return r == CUFFT_SUCCESS ? 0 : (int)r;
+}
+
+// half spectrum -> real, unnormalised (the multiply kernel applies 1/(L0 L1 L2)); overwrites W
+int spectral_inverse(SpectralShell *s, void *W, void *R) {
+    cufftResult r = s->fp64 ? s->api->z2d(s->plan[1], (cufftDoubleComplex *)W, (double *)R)
+                            : s->api->c2r(s->plan[1], (cufftComplex *)W, (float *)R);
+    return r == CUFFT_SUCCESS ? 0 : (int)r;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Cplx;
+template <>
+struct Cplx<float> {
+    using type = float2;
+};
+template <>
+struct Cplx<double> {
+    using type = double2;
+};
+
+// kappa_c(-e mod L) += e_c / |e| for every shell point (aliases on a short periodic axis add up)
+template <typename T>
+__global__ void k_spec_scatter(T *R3, long long Nr, int L0, int L1, int L2, const int *e, const double *u, int ne) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ne) return;
+    const int x = ((-e[3 * j] % L0) + L0) % L0;
+    const int y = ((-e[3 * j + 1] % L1) + L1) % L1;
+    const int z = ((-e[3 * j + 2] % L2) + L2) % L2;
+    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    for (int c = 0; c < 3; ++c) atomicAdd(&R3[(long long)c * Nr + idx], (T)u[3 * j + c]);
+}
+
+template <typename T>
+__global__ void k_spec_imag(const typename Cplx<T>::type *Z3, T *tab3, long long Nc) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nc) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) tab3[(long long)c * Nc + k] = Z3[(long long)c * Nc + k].y;
+}
+
+// one thread per grid point of a row: x = threadIdx + blockIdx.x * blockDim, y = blockIdx.y, z = blockIdx.z
+template <typename T>
+__global__ void k_spec_embed(Grid g, int L0, int L1, long long Nr, const T *__restrict__ npad,
+                             const T *__restrict__ gab, SpecPairs sp, T *__restrict__ R) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L0) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    const bool in = x < g.nx && y < g.ny && z < g.nz;
+    const long long pi = in ? pidx(g, x, y, z) : 0;
+    const long long i = in ? (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z) : 0;
+    for (int b = 0; b < sp.M; ++b) R[(long long)b * Nr + idx] = in ? npad[(long long)b * g.P + pi] : (T)0;
+    for (int q = 0; q < sp.npairs; ++q) {
+        T v = (T)0;
+        if (in) v = gab[(long long)(sp.a[q] * sp.M + sp.b[q]) * g.N + i] * npad[(long long)sp.b[q] * g.P + pi];
+        R[(long long)(sp.M + q) * Nr + idx] = v;
+    }
+}
+
+// W[3q + c] = i t_{S_q,c} n^_{b_q} scale ;  W[3 pairs + 3a + c] = sum_{q: a_q = a} coef_q / 2 i t_{S_q,c} G^_q scale
+template <typename T>
+__global__ void k_spec_multiply(const typename Cplx<T>::type *__restrict__ Z, const T *__restrict__ tab,
+                                typename Cplx<T>::type *__restrict__ W, long long Nc, SpecPairs sp, T scale) {
+    using C2 = typename Cplx<T>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nc) return;
+    for (int c = 0; c < 3; ++c) {
+        T qr[MAXS], qi[MAXS];
+        for (int a = 0; a < sp.M; ++a) qr[a] = qi[a] = (T)0;
+        for (int q = 0; q < sp.npairs; ++q) {
+            const T t = tab[((long long)sp.s[q] * 3 + c) * Nc + k] * scale;
+            const C2 nb = Z[(long long)sp.b[q] * Nc + k];
+            C2 o;
+            o.x = -t * nb.y;
+            o.y = t * nb.x;
+            W[((long long)3 * q + c) * Nc + k] = o;
+            const C2 gq = Z[(long long)(sp.M + q) * Nc + k];
+            const T w = (T)sp.half_coef[q] * t;
+            const int a = sp.a[q];
+            qr[a] -= w * gq.y;
+            qi[a] += w * gq.x;
+        }
+        for (int a = 0; a < sp.M; ++a) {
+            C2 o;
+            o.x = qr[a];
+            o.y = qi[a];
+            W[((long long)3 * sp.npairs + 3 * a + c) * Nc + k] = o;
+        }
+    }
+}
+
+// one thread per lattice node of a row: x = threadIdx + blockIdx.x * blockDim, y = blockIdx.y, z = blockIdx.z
+template <typename T>
+__global__ void k_spec_combine(Grid g, int L0, int L1, long long Nr, const T *__restrict__ R, const T *__restrict__ npad,
+                               const T *__restrict__ gab, SpecPairs sp, T *__restrict__ Cout, T *__restrict__ Pout) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    const long long ri = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    const long long pi = pidx(g, x, y, z);
+    for (int a = 0; a < sp.M; ++a) {
+        const T na = npad[(long long)a * g.P + pi];
+        for (int c = 0; c < 3; ++c) {
+            T v = R[((long long)3 * sp.npairs + 3 * a + c) * Nr + ri];
+            for (int q = 0; q < sp.npairs; ++q) {
+                if (sp.a[q] != a) continue;
+                const T Pq = R[((long long)3 * q + c) * Nr + ri];
+                v += (T)sp.half_coef[q] * gab[(long long)(a * sp.M + sp.b[q]) * g.N + i] * Pq;
+            }
+            Cout[((long long)a * 3 + c) * g.N + i] = na * v;
+        }
+    }
+    if (Pout)
+        for (int q = 0; q < sp.npairs; ++q)
+            for (int c = 0; c < 3; ++c)
+                Pout[((long long)q * 3 + c) * g.N + i] = R[((long long)3 * q + c) * Nr + ri];
+}
+
+namespace {
+constexpr int SNT = 256;
+constexpr int RNT = 128;  // threads along x of the row kernels (grid y and z: the rows)
+unsigned blocks(long long n) { return (unsigned)((n + SNT - 1) / SNT); }
+}  // namespace
+
+cudaError_t launch_spec_table(bool fp64, void *R3, long long Nr, const int L[3], const int *e, const double *u, int ne,
+                              cudaStream_t st) {
+    if (ne <= 0) return cudaSuccess;
+    if (fp64)
+        k_spec_scatter<double><<<blocks(ne), SNT, 0, st>>>((double *)R3, Nr, L[0], L[1], L[2], e, u, ne);
+    else
+        k_spec_scatter<float><<<blocks(ne), SNT, 0, st>>>((float *)R3, Nr, L[0], L[1], L[2], e, u, ne);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc, cudaStream_t st) {
+    if (fp64)
+        k_spec_imag<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z3, (double *)tab3, Nc);
+    else
+        k_spec_imag<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z3, (float *)tab3, Nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const void *npad,
+                              const void *gab, const SpecPairs &sp, void *R, cudaStream_t st) {
+    const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
+    if (fp64)
+        k_spec_embed<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const double *)npad, (const double *)gab, sp,
+                                                   (double *)R);
+    else
+        k_spec_embed<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const float *)npad, (const float *)gab, sp,
+                                                  (float *)R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc, const SpecPairs &sp,
+                                 double scale, cudaStream_t st) {
+    if (fp64)
+        k_spec_multiply<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z, (const double *)tab, (double2 *)W,
+                                                            Nc, sp, scale);
+    else
+        k_spec_multiply<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z, (const float *)tab, (float2 *)W, Nc,
+                                                           sp, (float)scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_combine(bool fp64, const Grid &g, const int L[3], long long Nr, const void *R,
+                                const void *npad, const void *gab, const SpecPairs &sp, void *Cout, void *Pout,
+                                cudaStream_t st) {
+    const dim3 grid((unsigned)((g.nx + RNT - 1) / RNT), (unsigned)g.ny, (unsigned)g.nz);
+    if (fp64)
+        k_spec_combine<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const double *)R, (const double *)npad,
+                                                     (const double *)gab, sp, (double *)Cout, (double *)Pout);
+    else
+        k_spec_combine<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const float *)R, (const float *)npad,
+                                                    (const float *)gab, sp, (float *)Cout, (float *)Pout);
+    return cudaGetLastError();
+}
+
+}  // namespace lbe

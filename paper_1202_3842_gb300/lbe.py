@@ -19,6 +19,8 @@ LIB_PATH = os.path.join(HERE, "liblbe.so")
 LBE_FP64, LBE_FP32, LBE_BF16_SHIFTED, LBE_FP16_SHIFTED = 0, 1, 2, 3
 LBE_DD_TR, LBE_SD_TR, LBE_SD_EU, LBE_DD_EU = 0, 1, 2, 3
 PRECISIONS = {"fp64": LBE_FP64, "fp32": LBE_FP32, "bf16": LBE_BF16_SHIFTED, "fp16": LBE_FP16_SHIFTED}
+(LBE_OK, LBE_ERR_INVALID_ARG, LBE_ERR_UNSUPPORTED, LBE_ERR_OOM, LBE_ERR_CUDA, LBE_ERR_DIVERGED, LBE_ERR_TIMEOUT,
+ LBE_ERR_STATE) = range(8)
 STATUS = {0: "LBE_OK", 1: "LBE_ERR_INVALID_ARG", 2: "LBE_ERR_UNSUPPORTED", 3: "LBE_ERR_OOM", 4: "LBE_ERR_CUDA",
           5: "LBE_ERR_DIVERGED", 6: "LBE_ERR_TIMEOUT", 7: "LBE_ERR_STATE"}
 
@@ -90,6 +92,8 @@ def lib():
             "lbe_load_state": [_P, _P, ctypes.c_size_t],
             "lbe_get_residual": [_P, _D],
             "lbe_get_divergence": [_P, ctypes.c_int, _D],
+            "lbe_set_shell_method": [_P, ctypes.c_int],
+            "lbe_get_shell_method": [_P, _I],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -345,6 +349,22 @@ def lbe_get_launch_count(ctx):
     return v.value
 
 
+SHELL_METHODS = {"auto": 0, "direct": 1, "spectral": 2}
+
+
+def lbe_set_shell_method(ctx, method):
+    """K3 method: "auto", "direct" (stencil sum) or "spectral" (FFT convolution)."""
+    m = SHELL_METHODS[method] if isinstance(method, str) else int(method)
+    _check(lib().lbe_set_shell_method(ctx, m), ctx)
+
+
+def lbe_get_shell_method(ctx):
+    """The K3 method the next step uses: "direct" or "spectral"."""
+    v = (ctypes.c_int * 1)()
+    _check(lib().lbe_get_shell_method(ctx, v), ctx)
+    return {1: "direct", 2: "spectral"}[v[0]]
+
+
 STAGES = ("density", "contact", "shell", "collide", "flux")
 
 
@@ -495,6 +515,12 @@ class Simulation:
 
     def adjoint_flux_gradient(self, nsteps, ckpt_every, axis, plane):
         return lbe_adjoint_flux_gradient(self._h, self.N, nsteps, ckpt_every, axis, plane)
+
+    def set_shell_method(self, method):
+        lbe_set_shell_method(self._h, method)
+
+    def shell_method(self):
+        return lbe_get_shell_method(self._h)
 
     def set_stage_timing(self, on):
         lbe_set_stage_timing(self._h, on)

@@ -20,11 +20,13 @@ def case_channel(shape, sigmas, eta, taus, width, length, body=1e-6, wall_amp_kT
 SCHEME_IDS = {"dd_tr": 0, "sd_tr": 1, "sd_eu": 2, "dd_eu": 3}
 
 
-def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_tr"):
+def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_tr", shell="auto"):
     from paper_1202_3842_gb300 import lbe
     M = len(w["sigma"])
     sim = lbe.Simulation(w["shape"], w["periodic"], M, precision, consistent_moments=consistent,
                          check_every=check_every, scheme=scheme)
+    if shell != "auto":
+        sim.set_shell_method(shell)
     sim.set_geometry(arrays["solid"])
     for a in range(M):
         sim.set_species(a, w["sigma"][a], w["tau"][a])

@@ -39,11 +39,13 @@ def _reference(w, arr, T, axis, plane, consistent=False):
                                             consistent=consistent)
 
 
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
 @pytest.mark.parametrize("consistent", [False, True])
-def test_fp64_adjoint_matches_reference(consistent):
+def test_fp64_adjoint_matches_reference(consistent, shell):
+    """The recomputation's force stage runs with either shell method; the transposes are the stencil's."""
     w, arr = _case()
     T, axis, plane = 8, 0, 8
-    g = setup_gpu(w, arr, "fp64", consistent=consistent)
+    g = setup_gpu(w, arr, "fp64", consistent=consistent, shell=shell)
     f0, g0 = g.populations(0)
     Phi, dA, dG = g.adjoint_flux_gradient(T, 3, axis, plane)
     rPhi, rA, rG = _reference(w, arr, T, axis, plane, consistent)

@@ -75,14 +75,16 @@ def test_populations_roundtrip_exact():
 # stage parity: contact values and shell force of a given state
 # ---------------------------------------------------------------------------
 
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
 @pytest.mark.parametrize("shape,sig", [((40, 22, 18), (2.0, 4.0)), ((37, 19, 35), (4.0, 6.0)),
                                        ((24, 24, 24), (3.0,))])
-def test_stage_parity_fp64(shape, sig):
+def test_stage_parity_fp64(shape, sig, shell):
     w, arr = case_channel(shape, sig, 0.25, (1.0,) * len(sig), 8, 10)
     rng = np.random.default_rng(8)
     fl = arr["solid"] == 0
     arr["n"] = arr["n"] * (1.0 + 0.2 * (rng.random(arr["n"].shape) - 0.5)) * fl[None, :]
-    g = setup_gpu(w, arr, "fp64")
+    g = setup_gpu(w, arr, "fp64", shell=shell)
+    assert g.shell_method() == shell
     o = setup_oracle(w, arr)
     obs = o.observe()
     M = len(sig)
@@ -94,8 +96,9 @@ def test_stage_parity_fp64(shape, sig):
         assert rel_err(C, obs["C"][a]) <= 1e-12
 
 
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
 @pytest.mark.parametrize("sig", [(1.0,), (2.0, 4.0), (4.0, 6.0), (6.0, 8.0), (8.0,), (3.0, 5.0)])
-def test_stage_parity_fp32_every_pair_diameter(sig):
+def test_stage_parity_fp32_every_pair_diameter(sig, shell):
     """K1-K3 of one FP32 state against the oracle for pair diameters 1 to 8 (the FP32 shell tiles: three
     outputs per thread along z up to 6, two at 7, one at 8) and both contact paths (compile-time balls for
     sigma 4/6, runtime rows otherwise, up to ball radius 4).  Tolerance: 1e-5 of the largest value of each
@@ -104,7 +107,8 @@ def test_stage_parity_fp32_every_pair_diameter(sig):
     rng = np.random.default_rng(9)
     fl = arr["solid"] == 0
     arr["n"] = arr["n"] * (1.0 + 0.2 * (rng.random(arr["n"].shape) - 0.5)) * fl[None, :]
-    g = setup_gpu(w, arr, "fp32")
+    g = setup_gpu(w, arr, "fp32", shell=shell)
+    assert g.shell_method() == shell
     o = setup_oracle(w, arr)
     obs = o.observe()
     M = len(sig)
@@ -119,10 +123,11 @@ def test_stage_parity_fp32_every_pair_diameter(sig):
 # FP64 dynamics
 # ---------------------------------------------------------------------------
 
-def test_fp64_parity_well24_200_steps():
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
+def test_fp64_parity_well24_200_steps(shell):
     """One-component spherical well, 24^3 periodic, sigma 3, eta 0.2, Gaussian well 1 kT / R 5, tau 1."""
     w, arr = case_well((24, 24, 24), 3.0, 0.2, 1.0, 1.0, 5.0)
-    g = setup_gpu(w, arr, "fp64")
+    g = setup_gpu(w, arr, "fp64", shell=shell)
     o = setup_oracle(w, arr)
     g.step(200)
     o.step(200)
@@ -135,9 +140,10 @@ def test_fp64_parity_well24_200_steps():
     assert np.abs(u_ref).max() / CS < 0.1  # spurious current stays small
 
 
-def test_fp64_parity_channel_mixture_with_flux():
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
+def test_fp64_parity_channel_mixture_with_flux(shell):
     w, arr = case_channel((48, 24, 20), (4.0, 6.0), 0.25, (1.0, 0.8), 10, 12, body=1e-5)
-    g = setup_gpu(w, arr, "fp64")
+    g = setup_gpu(w, arr, "fp64", shell=shell)
     o = setup_oracle(w, arr)
     g.set_flux_plane(0, 24)
     o.set_flux_plane(0, 24)
