@@ -282,6 +282,118 @@ __global__ void k_spec_combine(Grid g, int L0, int L1, long long Nr, const T *__
                 Pout[((long long)q * 3 + c) * g.N + i] = R[((long long)3 * q + c) * Nr + ri];
 }
 
+// The same three kernels for M = 1 or 2 species with all M^2 pairs present, in the order q = a M + b:
+// every loop has compile-time bounds, so the sums stay in registers.
+template <typename T, int M>
+__global__ void k_spec_embed_m(Grid g, int L0, int L1, long long Nr, const T *__restrict__ npad,
+                               const T *__restrict__ gab, T *__restrict__ R) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L0) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    T n[M], gn[M * M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) n[b] = (T)0;
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) gn[q] = (T)0;
+    if (x < g.nx && y < g.ny && z < g.nz) {
+        const long long pi = pidx(g, x, y, z);
+        const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+#pragma unroll
+        for (int b = 0; b < M; ++b) n[b] = npad[(long long)b * g.P + pi];
+#pragma unroll
+        for (int q = 0; q < M * M; ++q) gn[q] = gab[(long long)q * g.N + i] * n[q % M];
+    }
+#pragma unroll
+    for (int b = 0; b < M; ++b) R[(long long)b * Nr + idx] = n[b];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) R[(long long)(M + q) * Nr + idx] = gn[q];
+}
+
+template <typename T, int M>
+__global__ void k_spec_multiply_m(const typename Cplx<T>::type *__restrict__ Z, const T *__restrict__ tab,
+                                  typename Cplx<T>::type *__restrict__ W, long long Nc, SpecPairs sp, T scale) {
+    using C2 = typename Cplx<T>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nc) return;
+    C2 nh[M], gh[M * M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) nh[b] = Z[(long long)b * Nc + k];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) gh[q] = Z[(long long)(M + q) * Nc + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        T qr[M], qi[M];
+#pragma unroll
+        for (int a = 0; a < M; ++a) qr[a] = qi[a] = (T)0;
+#pragma unroll
+        for (int q = 0; q < M * M; ++q) {
+            const T t = tab[((long long)sp.s[q] * 3 + c) * Nc + k] * scale;
+            C2 o;
+            o.x = -t * nh[q % M].y;
+            o.y = t * nh[q % M].x;
+            W[((long long)3 * q + c) * Nc + k] = o;
+            const T w = (T)sp.half_coef[q] * t;
+            qr[q / M] -= w * gh[q].y;
+            qi[q / M] += w * gh[q].x;
+        }
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            C2 o;
+            o.x = qr[a];
+            o.y = qi[a];
+            W[((long long)3 * M * M + 3 * a + c) * Nc + k] = o;
+        }
+    }
+}
+
+template <typename T, int M>
+__global__ void k_spec_combine_m(Grid g, int L0, int L1, long long Nr, const T *__restrict__ R,
+                                 const T *__restrict__ npad, const T *__restrict__ gab, SpecPairs sp,
+                                 T *__restrict__ Cout, T *__restrict__ Pout) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    const long long ri = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    const long long pi = pidx(g, x, y, z);
+    T na[M], gq[M * M], P[M * M][3], Qs[M][3];
+#pragma unroll
+    for (int a = 0; a < M; ++a) na[a] = npad[(long long)a * g.P + pi];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q) gq[q] = gab[(long long)q * g.N + i];
+#pragma unroll
+    for (int q = 0; q < M * M; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) P[q][c] = R[((long long)3 * q + c) * Nr + ri];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Qs[a][c] = R[((long long)3 * M * M + 3 * a + c) * Nr + ri];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T v = Qs[a][c];
+#pragma unroll
+            for (int b = 0; b < M; ++b) v += (T)sp.half_coef[a * M + b] * gq[a * M + b] * P[a * M + b][c];
+            Cout[((long long)a * 3 + c) * g.N + i] = na[a] * v;
+        }
+    if (Pout)
+#pragma unroll
+        for (int q = 0; q < M * M; ++q)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) Pout[((long long)q * 3 + c) * g.N + i] = P[q][c];
+}
+
+// all M^2 pairs present in the order a M + b, M = 1 or 2
+bool full_pairs(const SpecPairs &sp) {
+    if (sp.M > 2 || sp.npairs != sp.M * sp.M) return false;
+    for (int q = 0; q < sp.npairs; ++q)
+        if (sp.a[q] != q / sp.M || sp.b[q] != q % sp.M) return false;
+    return true;
+}
+
 namespace {
 constexpr int SNT = 256;
 constexpr int RNT = 128;  // threads along x of the row kernels (grid y and z: the rows)
@@ -309,6 +421,17 @@ cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc
 cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const void *npad,
                               const void *gab, const SpecPairs &sp, void *R, cudaStream_t st) {
     const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
+    if (full_pairs(sp)) {
+#define LBE_SPEC_EMBED(TT, MM) \
+    k_spec_embed_m<TT, MM><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const TT *)npad, (const TT *)gab, (TT *)R)
+        if (fp64) {
+            if (sp.M == 1) LBE_SPEC_EMBED(double, 1); else LBE_SPEC_EMBED(double, 2);
+        } else {
+            if (sp.M == 1) LBE_SPEC_EMBED(float, 1); else LBE_SPEC_EMBED(float, 2);
+        }
+#undef LBE_SPEC_EMBED
+        return cudaGetLastError();
+    }
     if (fp64)
         k_spec_embed<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const double *)npad, (const double *)gab, sp,
                                                    (double *)R);
@@ -320,6 +443,18 @@ cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long lon
 
 cudaError_t launch_spec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc, const SpecPairs &sp,
                                  double scale, cudaStream_t st) {
+    if (full_pairs(sp)) {
+#define LBE_SPEC_MUL(TT, C2, MM)                                                                           \
+    k_spec_multiply_m<TT, MM><<<blocks(Nc), SNT, 0, st>>>((const C2 *)Z, (const TT *)tab, (C2 *)W, Nc, sp, \
+                                                          (TT)scale)
+        if (fp64) {
+            if (sp.M == 1) LBE_SPEC_MUL(double, double2, 1); else LBE_SPEC_MUL(double, double2, 2);
+        } else {
+            if (sp.M == 1) LBE_SPEC_MUL(float, float2, 1); else LBE_SPEC_MUL(float, float2, 2);
+        }
+#undef LBE_SPEC_MUL
+        return cudaGetLastError();
+    }
     if (fp64)
         k_spec_multiply<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z, (const double *)tab, (double2 *)W,
                                                             Nc, sp, scale);
@@ -333,6 +468,18 @@ cudaError_t launch_spec_combine(bool fp64, const Grid &g, const int L[3], long l
                                 const void *npad, const void *gab, const SpecPairs &sp, void *Cout, void *Pout,
                                 cudaStream_t st) {
     const dim3 grid((unsigned)((g.nx + RNT - 1) / RNT), (unsigned)g.ny, (unsigned)g.nz);
+    if (full_pairs(sp)) {
+#define LBE_SPEC_COMB(TT, MM)                                                                               \
+    k_spec_combine_m<TT, MM><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const TT *)R, (const TT *)npad,      \
+                                                   (const TT *)gab, sp, (TT *)Cout, (TT *)Pout)
+        if (fp64) {
+            if (sp.M == 1) LBE_SPEC_COMB(double, 1); else LBE_SPEC_COMB(double, 2);
+        } else {
+            if (sp.M == 1) LBE_SPEC_COMB(float, 1); else LBE_SPEC_COMB(float, 2);
+        }
+#undef LBE_SPEC_COMB
+        return cudaGetLastError();
+    }
     if (fp64)
         k_spec_combine<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const double *)R, (const double *)npad,
                                                      (const double *)gab, sp, (double *)Cout, (double *)Pout);
