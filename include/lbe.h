@@ -83,7 +83,7 @@ typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_
  *     the contact values (sigma_b / 2 <= 4);
  *   LBE_SHELL_AUTO (default): spectral for diameters without a compiled
  *     stencil, and where it is cheaper by a cost rule measured on GB300: the
- *     mean shell of the pairs above about 400 points (FP32 arithmetic) or 110
+ *     mean shell of the pairs above about 340 points (FP32 arithmetic) or 110
  *     points (FP64, where the stencil is bound by the FP64 rate), scaled by
  *     the padded grid over the lattice; direct otherwise.
  * Both give the sums of the definition up to rounding.  The adjoint
@@ -151,6 +151,18 @@ lbe_status lbe_set_wall_potential(lbe_ctx *ctx, const double *phi, const double 
 
 /* Uniform body force g[3] per unit mass on species s (Sec. "Channel flow"). */
 lbe_status lbe_set_body_force(lbe_ctx *ctx, int s, const double g[3]);
+
+/* Populations at rest with the quasi-pressure of Sec. "Stabilization" (the
+ * equation for Pi^alpha): f~_p = w_p n^a and g~_p = w_p Pi^a on fluid nodes,
+ *   Pi^a(r) = n^a(r) - beta * integral to r of (C^{a,mf} + n^a F^a) . dr',
+ * C^{a,mf} the mean-field force of the densities n, F^a the force field of the
+ * potentials set so far.  The integral is the trapezoidal rule along the
+ * lattice path from the origin along x (y = z = 0), then y (z = 0), then z
+ * (the paper leaves the path open; its constant never enters the evolution).
+ * n is [M][N], every species at once (all must be set with lbe_set_species);
+ * solid nodes are taken as n = 0.  Otherwise as lbe_init_density: sets the
+ * reference densities, resets the step counter and the flux average. */
+lbe_status lbe_init_density_quasipressure(lbe_ctx *ctx, const double *n);
 
 /* Choose the method of the shell force (lbe_shell_method; takes effect at the
  * next step).  LBE_ERR_INVALID_ARG for another value; LBE_ERR_UNSUPPORTED for

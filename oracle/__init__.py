@@ -46,6 +46,8 @@ def lib():
         L.or_shell_force.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_u8_p, ctypes.c_int, _c_dbl_p,
                                                           _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.or_force_field.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.or_quasipressure.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_u8_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
+                                                            _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.or_create.argtypes = [ctypes.c_int] * 7
         L.or_create.restype = ctypes.c_void_p
         L.or_destroy.argtypes = [ctypes.c_void_p]
@@ -171,6 +173,24 @@ def force_field(shape, periodic, V=None, gbody=(0.0, 0.0, 0.0)):
     lib().or_force_field(nx, ny, nz, _p(_per(periodic), ctypes.c_int), _p(Vp, ctypes.c_double),
                          _p(g, ctypes.c_double), _p(F, ctypes.c_double))
     return F
+
+
+def quasipressure(shape, periodic, sigma, n, V, gbody, solid=None):
+    """Pi^a = n^a - beta * trapezoidal path integral of C^{a,mf} + n^a F^a (x, then y, then z from the
+    origin); n and V [M, N] (V the full potential of each species), gbody [M, 3].  Returns [M, N]."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    n = _dbl(n).reshape(-1, N)
+    M = n.shape[0]
+    Vp = _dbl(V).reshape(M, N)
+    gb = _dbl(gbody).reshape(M, 3)
+    sig = _dbl(sigma)
+    out = np.zeros((M, N))
+    s = _solid(solid, N)
+    lib().or_quasipressure(nx, ny, nz, _p(_per(periodic), ctypes.c_int), _p(s, ctypes.c_uint8), M,
+                           _p(sig, ctypes.c_double), _p(n, ctypes.c_double), _p(Vp, ctypes.c_double),
+                           _p(gb, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
 
 
 class Sim:

@@ -333,6 +333,55 @@ void or_force_field(int nx, int ny, int nz, const int *per, const double *V, con
     }
 }
 
+/* Quasi-pressure of the second distribution (Sec. "Stabilization", equation
+ * for Pi^alpha): Pi^a = n^a - beta * integral to r of (C^{a,mf} + n^a F^a).dr',
+ * the integral by the trapezoidal rule along the lattice path from the origin:
+ * along x at y = z = 0, then along y at z = 0, then along z (the paper leaves
+ * the path open).  n [M][N] (taken as 0 on solid nodes), V [M][N] the full
+ * potential of each species, gbody [M][3]; C^{a,mf} from the contact values
+ * and shell sums of n.  Pi is [M][N]. */
+void or_quasipressure(int nx, int ny, int nz, const int *per, const uint8_t *solid, int M, const double *sigma,
+                      const double *n, const double *V, const double *gbody, double *Pi) {
+    grid_t g = {{nx, ny, nz}, {per[0], per[1], per[2]}};
+    long N = nsites(&g);
+    double *nn = (double *)malloc(sizeof(double) * M * N);
+    double *gp = (double *)malloc(sizeof(double) * M * M * N);
+    double *C = (double *)malloc(sizeof(double) * M * 3 * N);
+    double *F = (double *)malloc(sizeof(double) * 3 * N);
+    double *W = (double *)malloc(sizeof(double) * 3 * N);   /* C + n F of one species */
+    double *I = (double *)malloc(sizeof(double) * N);
+    for (long t = 0; t < (long)M * N; ++t) nn[t] = (solid && solid[t % N]) ? 0.0 : n[t];
+    or_contact_values(nx, ny, nz, per, solid, M, sigma, nn, gp);
+    or_shell_force(nx, ny, nz, per, solid, M, sigma, nn, gp, C);
+    for (int a = 0; a < M; ++a) {
+        const double *na = nn + (long)a * N;
+        or_force_field(nx, ny, nz, per, V + (long)a * N, gbody + 3 * a, F);
+        for (int c = 0; c < 3; ++c)
+            for (long i = 0; i < N; ++i) W[(long)c * N + i] = C[((long)a * 3 + c) * N + i] + na[i] * F[(long)c * N + i];
+        /* x at y = z = 0 */
+        I[0] = 0.0;
+        for (int x = 1; x < nx; ++x) {
+            long i1 = site(&g, x, 0, 0), i0 = site(&g, x - 1, 0, 0);
+            I[i1] = I[i0] + 0.5 * (W[i0] + W[i1]);
+        }
+        /* y at z = 0, for every x */
+        for (int x = 0; x < nx; ++x)
+            for (int y = 1; y < ny; ++y) {
+                long i1 = site(&g, x, y, 0), i0 = site(&g, x, y - 1, 0);
+                I[i1] = I[i0] + 0.5 * (W[N + i0] + W[N + i1]);
+            }
+        /* z, for every (x, y) */
+        for (int x = 0; x < nx; ++x)
+            for (int y = 0; y < ny; ++y)
+                for (int z = 1; z < nz; ++z) {
+                    long i1 = site(&g, x, y, z), i0 = site(&g, x, y, z - 1);
+                    I[i1] = I[i0] + 0.5 * (W[2 * N + i0] + W[2 * N + i1]);
+                }
+        for (long i = 0; i < N; ++i) Pi[(long)a * N + i] = na[i] - BETA * I[i];
+    }
+    free(nn); free(gp); free(C); free(F); free(W); free(I);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Simulation state                                                           */
 /* ------------------------------------------------------------------------- */

@@ -309,8 +309,9 @@ int shell_count(int S) {
 // Cost rule of LBE_SHELL_AUTO, from measurements on GB300 (512x128x128 two-species channel, pair
 // diameters 4, 5, 5, 6; 256^3 one-species well, diameter 6): the stencil costs a fixed time per node
 // and shell point, the spectral form a fixed time per grid point and pair (its transforms and
-// pointwise kernels), and the two break even at a mean shell of about 400 points per pair in FP32
-// (both workloads: 395 and 403) and about 110 in FP64, where the stencil is bound by the FP64 rate.
+// pointwise kernels), and the two break even at a mean shell of about 340 points per pair in FP32
+// (324 on the well, 355 on the channel) and about 110 in FP64, where the stencil is bound by the
+// FP64 rate.
 bool spectral_cheaper(const lbe_ctx *c, bool f64) {
     long long pts = 0;
     int Smax = 0;
@@ -322,7 +323,7 @@ bool spectral_cheaper(const lbe_ctx *c, bool f64) {
     const int n3[3] = {g.nx, g.ny, g.nz};
     double Nr = 1.0;
     for (int k = 0; k < 3; ++k) Nr *= g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
-    const double even = f64 ? 110.0 : 400.0;
+    const double even = f64 ? 110.0 : 340.0;
     return spectral_shape_ok(c, Smax) && (double)pts * (double)g.N > even * (double)c->pairs.size() * Nr;
 }
 
@@ -963,6 +964,59 @@ lbe_status lbe_init_density(lbe_ctx *c, int s, const double *n) {
     if (e != cudaSuccess) return cuda_fail(c, e, "init density");
     reset_counters(c);
     return LBE_OK;
+}
+
+lbe_status lbe_init_density_quasipressure(lbe_ctx *c, const double *n) {
+    TRY(ready(c));
+    if (!n) return fail(c, LBE_ERR_INVALID_ARG, "null density");
+    for (int a = 0; a < c->M; ++a)
+        if (!c->species_set[a]) return fail(c, LBE_ERR_STATE, "species " + std::to_string(a) + " not set");
+    const long long N = c->g.N;
+    const int M = c->M;
+    std::vector<double> nh((size_t)M * N);
+    for (int a = 0; a < M; ++a) {
+        double sum = 0.0;
+        long long cnt = 0;
+        for (long long i = 0; i < N; ++i) {
+            const double v = n[(long long)a * N + i];
+            if (!(v >= 0.0) || !std::isfinite(v)) return fail(c, LBE_ERR_INVALID_ARG, "density must be finite and >= 0");
+            nh[(size_t)a * N + i] = c->solid_h[i] ? 0.0 : v;
+            if (!c->solid_h[i]) {
+                sum += v;
+                ++cnt;
+            }
+        }
+        c->n0[a] = cnt > 0 ? sum / cnt : 0.0;
+        if ((c->prec == Prec::BF16 || c->prec == Prec::F16) && !(c->n0[a] > 0.0))
+            return fail(c, LBE_ERR_INVALID_ARG, "shifted storage needs a positive mean density");
+    }
+    Buf nd, pid;
+    auto done = [&](lbe_status st) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, nd);
+        dev_free(c, pid);
+        return st;
+    };
+    lbe_status st = dev_alloc(c, nd, 8 * (size_t)M * N);
+    if (st == LBE_OK) st = dev_alloc(c, pid, 8 * (size_t)M * N);
+    if (st != LBE_OK) return done(st);
+    cudaError_t e = cudaMemcpyAsync(nd.p, nh.data(), 8 * (size_t)M * N, cudaMemcpyHostToDevice, c->stream);
+    // the rest state of n, its force stage (C^mf of n), then Pi and the rest state with g from Pi
+    for (int a = 0; a < M && e == cudaSuccess; ++a, ++c->launches)
+        e = launch_rest_state(c->prec, c->g, (const uint32_t *)c->mask.p, (const double *)nd.p + (long long)a * N,
+                              c->pop[c->cur].p, a, c->n0[a], c->stream);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "init quasi-pressure"));
+    if ((st = prepare(c)) != LBE_OK || (st = force_stage(c)) != LBE_OK) return done(st);
+    e = launch_quasipressure(prec_fp64(c->prec), c->g, M, (const double *)nd.p, c->C.p, c->F.p, (double *)pid.p,
+                             c->stream);
+    c->launches += 4;
+    for (int a = 0; a < M && e == cudaSuccess; ++a, ++c->launches)
+        e = launch_rest_state(c->prec, c->g, (const uint32_t *)c->mask.p, (const double *)nd.p + (long long)a * N,
+                              c->pop[c->cur].p, a, c->n0[a], c->stream, (const double *)pid.p + (long long)a * N);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return done(cuda_fail(c, e, "init quasi-pressure"));
+    reset_counters(c);
+    return done(LBE_OK);
 }
 
 lbe_status lbe_step(lbe_ctx *c, int nsteps) {

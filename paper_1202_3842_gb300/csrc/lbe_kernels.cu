@@ -121,27 +121,30 @@ __global__ void k_unstream(Grid g, const uint32_t *__restrict__ mask, const doub
     }
 }
 
-// Rest state: streamed_p(r) = w_p n(r) on fluid nodes.
+// Rest state: streamed f_p(r) = w_p n(r) and g_p(r) = w_p Pi(r) on fluid nodes (Pi = n without pi).
 template <typename S, typename T>
 __global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const double *__restrict__ n,
-                             S *__restrict__ pop, int a, T n0) {
+                             const double *__restrict__ pi, S *__restrict__ pop, int a, T n0) {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     int x, y, z;
     node_xyz(g, s, x, y, z);
     const bool solid = mask[s] & 1u;
+    const double *gsrc = pi ? pi : n;
 #pragma unroll
     for (int p = 0; p < Q; ++p) {
-        double v = 0.0;
+        double v = 0.0, vg = 0.0;
         if (!solid) {
             int X = x + cx(p), Y = y + cy(p), Z = z + cz(p);
             bool ok = wrap(X, g.nx, g.per[0]) && wrap(Y, g.ny, g.per[1]) && wrap(Z, g.nz, g.per[2]);
             long long t = ok ? X + (long long)g.nx * (Y + (long long)g.ny * Z) : 0;
-            v = (ok && !(mask[t] & 1u)) ? wq(p) * n[t] : wq(p) * n[s];
+            const long long u = (ok && !(mask[t] & 1u)) ? t : s;
+            v = wq(p) * n[u];
+            vg = wq(p) * gsrc[u];
         }
         const T iwn0 = (T)1 / ((T)wq(p) * n0);
         Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)v, iwn0);
-        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)v, iwn0);
+        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)vg, iwn0);
     }
 }
 
@@ -186,9 +189,9 @@ cudaError_t launch_unstream(Prec p, const Grid &g, const uint32_t *mask, const d
 }
 
 cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
-                              double n0, cudaStream_t st) {
+                              double n0, cudaStream_t st, const double *pi) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
-    LBE_DISPATCH_PREC(p, (k_rest_state<S, T><<<nb, NT, 0, st>>>(g, mask, n, (S *)pop, a, (T)n0)));
+    LBE_DISPATCH_PREC(p, (k_rest_state<S, T><<<nb, NT, 0, st>>>(g, mask, n, pi, (S *)pop, a, (T)n0)));
     return cudaGetLastError();
 }
 

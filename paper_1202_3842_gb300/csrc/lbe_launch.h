@@ -88,8 +88,13 @@ cudaError_t launch_unstream(Prec p, const Grid &g, const uint32_t *mask, const d
                             void *pop, int a, double n0, cudaStream_t st);
 cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const void *pop, int a, double n0,
                               double *f, double *gq, cudaStream_t st);
+// pi (optional): the g distribution at rest from Pi [N] instead of n
 cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
-                              double n0, cudaStream_t st);
+                              double n0, cudaStream_t st, const double *pi = nullptr);
+// Quasi-pressure Pi^a = n^a - beta * path integral of C^{a,mf} + n^a F^a (lbe_quasipressure.cu):
+// n [M][N] FP64, C and F [M][3][N] in the compute type; Pi [M][N] FP64.
+cudaError_t launch_quasipressure(bool fp64, const Grid &g, int M, const double *n, const void *C, const void *F,
+                                 double *Pi, cudaStream_t st);
 // K1: density (pulled zeroth moment) of every species into the padded field.
 // solid = false: no solid node and every axis periodic (the link mask is not read).
 cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,

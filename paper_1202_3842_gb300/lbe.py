@@ -93,6 +93,7 @@ def lib():
             "lbe_get_residual": [_P, _D],
             "lbe_get_divergence": [_P, ctypes.c_int, _D],
             "lbe_set_shell_method": [_P, ctypes.c_int],
+            "lbe_init_density_quasipressure": [_P, _D],
             "lbe_get_shell_method": [_P, _I],
         }
         for name, args in sig.items():
@@ -349,6 +350,12 @@ def lbe_get_launch_count(ctx):
     return v.value
 
 
+def lbe_init_density_quasipressure(ctx, M, N, n):
+    """Rest populations with g from the quasi-pressure path integral; n is [M][N] (FP64)."""
+    a = np.ascontiguousarray(np.asarray(n, dtype=np.float64).reshape(M, N))
+    _check(lib().lbe_init_density_quasipressure(ctx, _dp(a)), ctx)
+
+
 SHELL_METHODS = {"auto": 0, "direct": 1, "spectral": 2}
 
 
@@ -515,6 +522,9 @@ class Simulation:
 
     def adjoint_flux_gradient(self, nsteps, ckpt_every, axis, plane):
         return lbe_adjoint_flux_gradient(self._h, self.N, nsteps, ckpt_every, axis, plane)
+
+    def init_density_quasipressure(self, n):
+        lbe_init_density_quasipressure(self._h, self.M, self.N, n)
 
     def set_shell_method(self, method):
         lbe_set_shell_method(self._h, method)
