@@ -608,6 +608,13 @@ def run_ours(args):
                          "depth (oracle and GPU agree), so no longer window is physical" % (5 + k))
         result["well256_bounded"] = extra
 
+    if not args.no_extra and args.prec != "fp64":
+        # the same workload with FP64 populations (K3 in the spectral form the cost rule picks for FP64)
+        k = min(10, args.steps)
+        extra, _, _ = measure(args, args.workload, "fp64", k, 3, dist, world, local, peaks, peaks_kind)
+        extra["note"] = "FP64 storage and arithmetic, %d steps after 3 warm-up" % k
+        result["fp64_same_workload"] = extra
+
     if not args.no_extra and args.prec in ("fp32", "fp64"):
         result["adjoint"] = measure_adjoint(args.prec, T=args.adjoint_steps, K=args.adjoint_ckpt)
 
