@@ -79,11 +79,12 @@ typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_
  *     storage) or 1..7 (FP64);
  *   LBE_SHELL_SPECTRAL: the same sums as circular convolutions by fast
  *     Fourier transforms (cuFFT, loaded at run time) on a grid padded with
- *     zeros along closed axes; any integer pair diameter up to the limit of
- *     the contact values (sigma_b / 2 <= 4);
+ *     zeros along closed axes, and the ball averages of the contact values
+ *     likewise; any integer pair diameter up to the limit of the contact
+ *     values (sigma_b / 2 <= 4);
  *   LBE_SHELL_AUTO (default): spectral for diameters without a compiled
  *     stencil, and where it is cheaper by a cost rule measured on GB300: the
- *     mean shell of the pairs above about 340 points (FP32 arithmetic) or 110
+ *     mean shell of the pairs above about 320 points (FP32 arithmetic) or 110
  *     points (FP64, where the stencil is bound by the FP64 rate), scaled by
  *     the padded grid over the lattice; direct otherwise.
  * Both give the sums of the definition up to rounding.  The adjoint

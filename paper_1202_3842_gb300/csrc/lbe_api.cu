@@ -89,6 +89,7 @@ struct lbe_ctx {
     SpectralShell *spec = nullptr;
     int specL[3] = {0, 0, 0};
     long long specNr = 0, specNc = 0;
+    int specNS = 0;  // shells with a spectrum; the ball spectra follow them in specTab
     SpecPairs specPairs{};
     Buf specR, specZ, specW, specTab, specWork;
 
@@ -307,11 +308,12 @@ int shell_count(int S) {
 }
 
 // Cost rule of LBE_SHELL_AUTO, from measurements on GB300 (512x128x128 two-species channel, pair
-// diameters 4, 5, 5, 6; 256^3 one-species well, diameter 6): the stencil costs a fixed time per node
-// and shell point, the spectral form a fixed time per grid point and pair (its transforms and
-// pointwise kernels), and the two break even at a mean shell of about 340 points per pair in FP32
-// (324 on the well, 355 on the channel) and about 110 in FP64, where the stencil is bound by the
-// FP64 rate.
+// diameters 4, 5, 5, 6; 256^3 one-species well, diameter 6).  The spectral form replaces the contact
+// kernel and the shell stencil; the stencil costs a fixed time per node and shell point, the spectral
+// form a fixed time per grid point and pair.  Counting the contact kernel's time on the direct side,
+// the two break even at a mean shell of about 280 (well) to 323 (channel) points per pair in FP32,
+// scaled by the lattice over the grid, and about 100 in FP64, where the stencil is bound by the FP64
+// rate.  The constants lean to the stencil.
 bool spectral_cheaper(const lbe_ctx *c, bool f64) {
     long long pts = 0;
     int Smax = 0;
@@ -323,7 +325,7 @@ bool spectral_cheaper(const lbe_ctx *c, bool f64) {
     const int n3[3] = {g.nx, g.ny, g.nz};
     double Nr = 1.0;
     for (int k = 0; k < 3; ++k) Nr *= g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
-    const double even = f64 ? 110.0 : 340.0;
+    const double even = f64 ? 110.0 : 320.0;
     return spectral_shape_ok(c, Smax) && (double)pts * (double)g.N > even * (double)c->pairs.size() * Nr;
 }
 
@@ -354,18 +356,20 @@ lbe_status spectral_setup(lbe_ctx *c) {
     for (int k = 0; k < 3; ++k) L[k] = g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
     if (!spectral_shape_ok(c, Smax))
         return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: an axis of the grid is longer than 65535");
-    const int nfwd = c->M + sp.npairs, ninv = 3 * sp.npairs + 3 * c->M, nS = (int)shells.size();
+    const int M = c->M, nfwd = M + sp.npairs, ninv = 3 * sp.npairs + 3 * M, nS = (int)shells.size();
     spectral_destroy(c->spec);
     c->spec = nullptr;
     std::string why;
     size_t ws = 0;
-    if (spectral_create(&c->spec, f64, L, nfwd, ninv, &ws, &why) != 0)
+    if (spectral_create(&c->spec, f64, L, M, sp.npairs, ninv, &ws, &why) != 0)
         return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: " + why);
     const long long Nr = (long long)L[0] * L[1] * L[2], Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
-    TRY(dev_alloc(c, c->specR, rb * (size_t)std::max(ninv, std::max(nfwd, 3)) * Nr));
+    // real fields: the densities, the pairs' g n and the ball averages, later the ninv force fields
+    TRY(dev_alloc(c, c->specR, rb * (size_t)std::max(ninv, std::max(nfwd + M, 3)) * Nr));
     TRY(dev_alloc(c, c->specZ, 2 * rb * (size_t)std::max(nfwd, 3) * Nc));
     TRY(dev_alloc(c, c->specW, 2 * rb * (size_t)ninv * Nc));
-    TRY(dev_alloc(c, c->specTab, rb * 3 * (size_t)nS * Nc));
+    // tables: t_c of every shell [nS][3][Nc], then the ball spectrum of every species [M][Nc]
+    TRY(dev_alloc(c, c->specTab, rb * (size_t)(3 * nS + M) * Nc));
     TRY(dev_alloc(c, c->specWork, ws));
     if (spectral_bind(c->spec, c->specWork.p, c->stream) != 0)
         return fail(c, LBE_ERR_CUDA, "spectral shell force: binding the cuFFT work area failed");
@@ -373,21 +377,35 @@ lbe_status spectral_setup(lbe_ctx *c) {
     c->specNr = Nr;
     c->specNc = Nc;
     c->specPairs = sp;
-    // shell spectra t_c = Im FFT(kappa_c), kappa_c(-e mod L) = e_c / |e|
-    std::vector<std::vector<int>> eh(nS);
-    std::vector<std::vector<double>> uh(nS);
-    std::vector<Buf> ed(nS), ud(nS);
+    // shell spectra t_c = Im FFT(kappa_c), kappa_c(-e mod L) = e_c / |e|; ball spectra Re FFT(beta_b),
+    // beta_b(-d mod L) = 1 / |B_b| on the ball rows of the contact kernel (even, so the spectrum is real)
+    const int ntab = nS + M;
+    std::vector<std::vector<int>> eh(ntab);
+    std::vector<std::vector<double>> uh(ntab);
+    std::vector<Buf> ed(ntab), ud(ntab);
     lbe_status st = LBE_OK;
-    for (int s = 0; s < nS && st == LBE_OK; ++s) {
-        const int S = shells[s];
-        for (int z = -S; z <= S; ++z)
-            for (int y = -S; y <= S; ++y)
-                for (int x = -S; x <= S; ++x)
-                    if (in_shell(S, x, y, z)) {
-                        const double len = std::sqrt((double)(x * x + y * y + z * z));
-                        eh[s].insert(eh[s].end(), {x, y, z});
-                        uh[s].insert(uh[s].end(), {x / len, y / len, z / len});
+    for (int s = 0; s < ntab && st == LBE_OK; ++s) {
+        if (s < nS) {
+            const int S = shells[s];
+            for (int z = -S; z <= S; ++z)
+                for (int y = -S; y <= S; ++y)
+                    for (int x = -S; x <= S; ++x)
+                        if (in_shell(S, x, y, z)) {
+                            const double len = std::sqrt((double)(x * x + y * y + z * z));
+                            eh[s].insert(eh[s].end(), {x, y, z});
+                            uh[s].insert(uh[s].end(), {x / len, y / len, z / len});
+                        }
+        } else {
+            const int b = s - nS;
+            const BallRows &br = c->brows;
+            const double w = 1.0 / br.count[b];
+            for (int dz = -4; dz <= 4; ++dz)
+                for (int k = br.first[b][dz + 4]; k < br.first[b][dz + 5]; ++k)
+                    for (int dx = -br.a[b][k]; dx <= br.a[b][k]; ++dx) {
+                        eh[s].insert(eh[s].end(), {dx, (int)br.dy[b][k], dz});
+                        uh[s].insert(uh[s].end(), {w, 0.0, 0.0});
                     }
+        }
         const int ne = (int)(eh[s].size() / 3);
         if ((st = dev_alloc(c, ed[s], sizeof(int) * eh[s].size())) != LBE_OK) break;
         if ((st = dev_alloc(c, ud[s], sizeof(double) * uh[s].size())) != LBE_OK) break;
@@ -408,12 +426,17 @@ lbe_status spectral_setup(lbe_ctx *c) {
             st = fail(c, LBE_ERR_CUDA, "spectral shell tables: cuFFT forward transform failed");
             break;
         }
-        e = launch_spec_imag(f64, c->specZ.p, (char *)c->specTab.p + rb * 3 * (size_t)s * Nc, Nc, c->stream);
+        if (s < nS)
+            e = launch_spec_imag(f64, c->specZ.p, (char *)c->specTab.p + rb * 3 * (size_t)s * Nc, Nc, c->stream);
+        else
+            e = launch_spec_real(f64, c->specZ.p, (char *)c->specTab.p + rb * (size_t)(3 * nS + s - nS) * Nc, Nc,
+                                 c->stream);
         c->launches += 1;
         if (e != cudaSuccess) st = cuda_fail(c, e, "spectral shell tables");
     }
+    c->specNS = nS;
     cudaError_t e = cudaStreamSynchronize(c->stream);  // the host lists must outlive their copies
-    for (int s = 0; s < nS; ++s) {
+    for (int s = 0; s < ntab; ++s) {
         dev_free(c, ed[s]);
         dev_free(c, ud[s]);
     }
@@ -422,21 +445,39 @@ lbe_status spectral_setup(lbe_ctx *c) {
     return LBE_OK;
 }
 
-// K3 in spectral form for every pair: C [M][3][N] (and P [npairs][3][N] into Pbase for the adjoint).
-lbe_status spectral_shell(lbe_ctx *c, void *Pbase) {
+// K2 and K3 in spectral form: g_ab [M][M][N] (xi2, xi3 into xibase for the adjoint) and C [M][3][N]
+// (P [npairs][3][N] into Pbase for the adjoint).  Real fields in specR: the densities [M], the pairs'
+// g n [npairs], the ball averages [M]; then the force fields [ninv].
+lbe_status spectral_force(lbe_ctx *c, void *Pbase, void *xibase) {
     const bool f64 = prec_fp64(c->prec);
-    LAUNCH(launch_spec_embed(f64, c->g, c->specL, c->specNr, c->npad.p, c->gab.p, c->specPairs, c->specR.p,
-                             c->stream),
-           "spectral embed");
-    if (spectral_forward(c->spec, 0, c->specR.p, c->specZ.p) != 0)
+    const size_t rb = real_bytes(c);
+    const int M = c->M, np = c->specPairs.npairs;
+    const long long Nr = c->specNr, Nc = c->specNc;
+    char *R = (char *)c->specR.p, *Z = (char *)c->specZ.p, *W = (char *)c->specW.p;
+    const double scale = 1.0 / (double)Nr;
+    {
+        StageTimer t(c, LBE_STAGE_CONTACT);
+        LAUNCH(launch_spec_embed_n(f64, c->g, c->specL, Nr, M, c->npad.p, R, c->stream), "spectral embed");
+        if (spectral_forward(c->spec, 0, R, Z) != 0)
+            return fail(c, LBE_ERR_CUDA, "spectral contact values: cuFFT forward transform failed");
+        LAUNCH(launch_spec_ball_mul(f64, Z, (const char *)c->specTab.p + rb * 3 * (size_t)c->specNS * Nc, W, Nc, M,
+                                    scale, c->stream),
+               "spectral ball average");
+        char *nbar = R + rb * (size_t)(M + np) * Nr;
+        if (spectral_inverse(c->spec, 4, W, nbar) != 0)
+            return fail(c, LBE_ERR_CUDA, "spectral contact values: cuFFT inverse transform failed");
+        LAUNCH(launch_spec_contact(f64, c->g, c->specL, Nr, c->cparams, c->specPairs, c->npad.p, nbar, c->gab.p,
+                                   xibase, R + rb * (size_t)M * Nr, (int *)c->err.p, c->stream),
+               "spectral contact values");
+    }
+    StageTimer t(c, LBE_STAGE_SHELL);
+    if (spectral_forward(c->spec, 3, R + rb * (size_t)M * Nr, Z + 2 * rb * (size_t)M * Nc) != 0)
         return fail(c, LBE_ERR_CUDA, "spectral shell force: cuFFT forward transform failed");
-    LAUNCH(launch_spec_multiply(f64, c->specZ.p, c->specTab.p, c->specW.p, c->specNc, c->specPairs,
-                                1.0 / (double)c->specNr, c->stream),
-           "spectral multiply");
-    if (spectral_inverse(c->spec, c->specW.p, c->specR.p) != 0)
+    LAUNCH(launch_spec_multiply(f64, Z, c->specTab.p, W, Nc, c->specPairs, scale, c->stream), "spectral multiply");
+    if (spectral_inverse(c->spec, 1, W, R) != 0)
         return fail(c, LBE_ERR_CUDA, "spectral shell force: cuFFT inverse transform failed");
-    LAUNCH(launch_spec_combine(f64, c->g, c->specL, c->specNr, c->specR.p, c->npad.p, c->gab.p, c->specPairs,
-                               c->C.p, Pbase, c->stream),
+    LAUNCH(launch_spec_combine(f64, c->g, c->specL, Nr, R, c->npad.p, c->gab.p, c->specPairs, c->C.p, Pbase,
+                               c->stream),
            "spectral combine");
     return LBE_OK;
 }
@@ -533,16 +574,17 @@ lbe_status prepare(lbe_ctx *c) {
         c->cparams = cp;
         const size_t rb = real_bytes(c);
         TRY(dev_alloc(c, c->npad, rb * c->M * g.P));
-        // g_ab n_b of every ordered pair: FP32 stores the interleaved pair (n_b, g_ab n_b), 8 bytes per node
+        // g_ab n_b of every ordered pair for the direct shell stencil: FP32 stores the interleaved pair
+        // (n_b, g_ab n_b), 8 bytes per node (the spectral form keeps its own grid fields instead)
         const size_t gnb = (f64 ? rb : 2 * rb) * c->M * c->M * g.P;
-        TRY(dev_alloc(c, c->gnpad, gnb));
+        if (!c->spectral) TRY(dev_alloc(c, c->gnpad, gnb));
         TRY(dev_alloc(c, c->gab, rb * c->M * c->M * g.N));
         TRY(dev_alloc(c, c->C, rb * c->M * 3 * g.N));
         CK(cudaMemsetAsync(c->npad.p, 0, rb * c->M * g.P, c->stream), "memset npad");
-        CK(cudaMemsetAsync(c->gnpad.p, 0, gnb, c->stream), "memset gnpad");
+        if (!c->spectral) CK(cudaMemsetAsync(c->gnpad.p, 0, gnb, c->stream), "memset gnpad");
         CK(cudaMemsetAsync(c->C.p, 0, rb * c->M * 3 * g.N, c->stream), "memset C");
         for (auto &ps : c->pairs) {
-            if (!shell_supported(f64, ps.S)) continue;  // spectral only
+            if (c->spectral) break;
             char *nb = (char *)c->npad.p + rb * ps.b * g.P;
             char *gn = (char *)c->gnpad.p + (f64 ? rb : 2 * rb) * (ps.a * c->M + ps.b) * g.P;
             int bx = 0, by = 0;
@@ -605,6 +647,7 @@ lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = null
                "density kernel");
     }
     if (c->pairs.empty()) return LBE_OK;  // ideal gas: C stays zero
+    if (c->spectral) return spectral_force(c, Pbase, xibase);
     {
         StageTimer t(c, LBE_STAGE_CONTACT);
         ContactLaunch L{};
@@ -618,10 +661,6 @@ lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = null
         L.xi = xibase;
         L.err = (int *)c->err.p;
         LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
-    }
-    if (c->spectral) {
-        StageTimer t(c, LBE_STAGE_SHELL);
-        return spectral_shell(c, Pbase);
     }
     std::vector<int> first(c->M, 1);
     for (size_t q = 0; q < c->pairs.size(); ++q) {

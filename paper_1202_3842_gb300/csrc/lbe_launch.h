@@ -214,19 +214,26 @@ struct SpecPairs {
 };
 struct SpectralShell;  // cuFFT plans of one lattice
 bool spectral_available(std::string *why);
-// Plans for the grid L (x fastest): forward of nfwd real fields, inverse of ninv half spectra, and a
-// three-field forward for the shell tables.  Returns 0, or -1 with the reason in *why.
-int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, int ninv, size_t *work_bytes,
+// Plans for the grid L (x fastest): forward of the M densities (0), inverse of ninv force spectra (1),
+// forward of three table fields (2), forward of the npairs fields g n (3), inverse of the M ball
+// averages (4).  Returns 0, or -1 with the reason in *why.
+int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int npairs, int ninv, size_t *work_bytes,
                     std::string *why);
 void spectral_destroy(SpectralShell *s);
 int spectral_bind(SpectralShell *s, void *work, cudaStream_t st);
-int spectral_forward(SpectralShell *s, int which /* 0: nfwd fields, 2: three table fields */, void *R, void *Z);
-int spectral_inverse(SpectralShell *s, void *W, void *R);
+int spectral_forward(SpectralShell *s, int which /* 0, 2 or 3 */, void *R, void *Z);
+int spectral_inverse(SpectralShell *s, int which /* 1 or 4 */, void *W, void *R);
 cudaError_t launch_spec_table(bool fp64, void *R3, long long Nr, const int L[3], const int *e, const double *u, int ne,
                               cudaStream_t st);
 cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc, cudaStream_t st);
-cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const void *npad,
-                              const void *gab, const SpecPairs &sp, void *R, cudaStream_t st);
+cudaError_t launch_spec_real(bool fp64, const void *Z, void *tab, long long Nc, cudaStream_t st);
+cudaError_t launch_spec_embed_n(bool fp64, const Grid &g, const int L[3], long long Nr, int M, const void *npad,
+                                void *R, cudaStream_t st);
+cudaError_t launch_spec_ball_mul(bool fp64, const void *Z, const void *btab, void *W, long long Nc, int M,
+                                 double scale, cudaStream_t st);
+cudaError_t launch_spec_contact(bool fp64, const Grid &g, const int L[3], long long Nr, const ContactParams &cp,
+                                const SpecPairs &sp, const void *npad, const void *nbar, void *gab, void *xi, void *G,
+                                int *err, cudaStream_t st);
 cudaError_t launch_spec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc, const SpecPairs &sp,
                                  double scale, cudaStream_t st);
 cudaError_t launch_spec_combine(bool fp64, const Grid &g, const int L[3], long long Nr, const void *R,

@@ -8,13 +8,17 @@
 // kappa(x) = K_S(-x mod L), so
 //   P^(k) = kappa^(k) n^(k),   kappa^(k) = i t(k),
 // t real because kappa is real and odd.  The three components of t are tabulated once per shell by
-// transforming kappa itself.  One force stage then runs
-//   1. k_spec_embed: n_b and g_ab n_b of every pair into the zero-padded grid;
-//   2. one batched forward transform of those M + pairs fields;
-//   3. k_spec_multiply: the P spectra of every pair and component, and per species the Q spectra
+// transforming kappa itself.  The ball averages of the contact values (n-bar_b, the mean of n_b over
+// |d| <= sigma_b / 2) are convolutions with a real, even kernel, whose transform is real and is
+// tabulated the same way.  One force stage (after K1) then runs
+//   1. k_spec_embed_n: n_b into the zero-padded grid, one batched forward transform;
+//   2. k_spec_ball_mul and one batched inverse transform: n-bar_b;
+//   3. k_spec_contact: xi_2, xi_3 and the BMCSL g_ab of every node as in the direct contact kernel,
+//      and g_ab n_b of every pair into the grid; one batched forward transform of those;
+//   4. k_spec_multiply: the P spectra of every pair and component, and per species the Q spectra
 //      summed with coef_ab / 2 (the inverse transform is linear), scaled by 1 / (L0 L1 L2);
-//   4. one batched inverse transform of the 3 pairs + 3 M spectra;
-//   5. k_spec_combine: C^a(r) = n_a(r) [ sum_b coef_ab / 2 g_ab(r) P_ab(r) + Qsum_a(r) ], the
+//   5. one batched inverse transform of the 3 pairs + 3 M spectra;
+//   6. k_spec_combine: C^a(r) = n_a(r) [ sum_b coef_ab / 2 g_ab(r) P_ab(r) + Qsum_a(r) ], the
 //      arithmetic of the direct kernel regrouped (and P itself when the adjoint keeps it).
 // The transforms are cuFFT's (a library FFT, like a library GEMM), loaded at run time from
 // libcufft.so.12 so that the library still needs only libcuda to load; without it the spectral
@@ -95,20 +99,23 @@ struct SpectralShell {
     bool fp64 = false;
     int L[3] = {0, 0, 0};
     long long Nr = 0, Nc = 0;
-    cufftHandle plan[3] = {0, 0, 0};  // forward (nfwd fields), inverse (ninv), table (3 fields)
-    bool made[3] = {false, false, false};
+    // 0: forward of the M densities; 1: inverse of the 3 pairs + 3 M force spectra; 2: forward of three
+    // table fields; 3: forward of the pairs' g n; 4: inverse of the M ball averages
+    static constexpr int NPLAN = 5;
+    cufftHandle plan[NPLAN] = {0, 0, 0, 0, 0};
+    bool made[NPLAN] = {false, false, false, false, false};
 };
 
 bool spectral_available(std::string *why) { return cufft_api(why) != nullptr; }
 
 void spectral_destroy(SpectralShell *s) {
     if (!s) return;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < SpectralShell::NPLAN; ++k)
         if (s->made[k]) s->api->destroy(s->plan[k]);
     delete s;
 }
 
-int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, int ninv, size_t *work_bytes,
+int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int npairs, int ninv, size_t *work_bytes,
                     std::string *why) {
     *out = nullptr;
     const CufftApi *api = cufft_api(why);
@@ -120,11 +127,11 @@ int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, in
     s->Nr = (long long)L[0] * L[1] * L[2];
     s->Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
     int n[3] = {L[2], L[1], L[0]};  // row-major: x is the fastest (and the halved) dimension
-    const int batch[3] = {nfwd, ninv, 3};
-    const cufftType type[3] = {fp64 ? CUFFT_D2Z : CUFFT_R2C, fp64 ? CUFFT_Z2D : CUFFT_C2R,
-                               fp64 ? CUFFT_D2Z : CUFFT_R2C};
+    const int batch[SpectralShell::NPLAN] = {M, ninv, 3, npairs, M};
+    const cufftType fwd = fp64 ? CUFFT_D2Z : CUFFT_R2C, inv = fp64 ? CUFFT_Z2D : CUFFT_C2R;
+    const cufftType type[SpectralShell::NPLAN] = {fwd, inv, fwd, fwd, inv};
     size_t wmax = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < SpectralShell::NPLAN; ++k) {
         cufftResult r = api->create(&s->plan[k]);
         if (r != CUFFT_SUCCESS) {
             if (why) *why = "cufftCreate failed (" + std::to_string((int)r) + ")";
@@ -148,24 +155,25 @@ int spectral_create(SpectralShell **out, bool fp64, const int L[3], int nfwd, in
 }
 
 int spectral_bind(SpectralShell *s, void *work, cudaStream_t st) {
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < SpectralShell::NPLAN; ++k) {
         if (s->api->set_work(s->plan[k], work) != CUFFT_SUCCESS) return -1;
         if (s->api->set_stream(s->plan[k], st) != CUFFT_SUCCESS) return -1;
     }
     return 0;
 }
 
-// which: 0 forward (nfwd fields), 2 table (3 fields); real -> half spectrum
+// which: 0 the densities, 2 three table fields, 3 the pairs' g n; real -> half spectrum
 int spectral_forward(SpectralShell *s, int which, void *R, void *Z) {
     cufftResult r = s->fp64 ? s->api->d2z(s->plan[which], (double *)R, (cufftDoubleComplex *)Z)
                             : s->api->r2c(s->plan[which], (float *)R, (cufftComplex *)Z);
     return r == CUFFT_SUCCESS ? 0 : (int)r;
 }
 
-// half spectrum -> real, unnormalised (the multiply kernel applies 1/(L0 L1 L2)); overwrites W
-int spectral_inverse(SpectralShell *s, void *W, void *R) {
-    cufftResult r = s->fp64 ? s->api->z2d(s->plan[1], (cufftDoubleComplex *)W, (double *)R)
-                            : s->api->c2r(s->plan[1], (cufftComplex *)W, (float *)R);
+// which: 1 the force spectra, 4 the ball averages; half spectrum -> real, unnormalised (the multiply
+// kernels apply 1/(L0 L1 L2)); overwrites W
+int spectral_inverse(SpectralShell *s, int which, void *W, void *R) {
+    cufftResult r = s->fp64 ? s->api->z2d(s->plan[which], (cufftDoubleComplex *)W, (double *)R)
+                            : s->api->c2r(s->plan[which], (cufftComplex *)W, (float *)R);
     return r == CUFFT_SUCCESS ? 0 : (int)r;
 }
 
@@ -203,22 +211,92 @@ __global__ void k_spec_imag(const typename Cplx<T>::type *Z3, T *tab3, long long
     for (int c = 0; c < 3; ++c) tab3[(long long)c * Nc + k] = Z3[(long long)c * Nc + k].y;
 }
 
+template <typename T>
+__global__ void k_spec_real(const typename Cplx<T>::type *Z, T *tab, long long Nc) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < Nc) tab[k] = Z[k].x;
+}
+
 // one thread per grid point of a row: x = threadIdx + blockIdx.x * blockDim, y = blockIdx.y, z = blockIdx.z
 template <typename T>
-__global__ void k_spec_embed(Grid g, int L0, int L1, long long Nr, const T *__restrict__ npad,
-                             const T *__restrict__ gab, SpecPairs sp, T *__restrict__ R) {
+__global__ void k_spec_embed_n(Grid g, int L0, int L1, long long Nr, int M, const T *__restrict__ npad,
+                               T *__restrict__ R) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= L0) return;
     const int y = blockIdx.y, z = blockIdx.z;
     const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
     const bool in = x < g.nx && y < g.ny && z < g.nz;
     const long long pi = in ? pidx(g, x, y, z) : 0;
-    const long long i = in ? (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z) : 0;
-    for (int b = 0; b < sp.M; ++b) R[(long long)b * Nr + idx] = in ? npad[(long long)b * g.P + pi] : (T)0;
+    for (int b = 0; b < M; ++b) R[(long long)b * Nr + idx] = in ? npad[(long long)b * g.P + pi] : (T)0;
+}
+
+// W[b] = n^_b B^_b scale: the spectrum of the ball average (B^ real: the ball kernel is even)
+template <typename T>
+__global__ void k_spec_ball_mul(const typename Cplx<T>::type *__restrict__ Z, const T *__restrict__ btab,
+                                typename Cplx<T>::type *__restrict__ W, long long Nc, int M, T scale) {
+    using C2 = typename Cplx<T>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nc) return;
+    for (int b = 0; b < M; ++b) {
+        const T w = btab[(long long)b * Nc + k] * scale;
+        const C2 z = Z[(long long)b * Nc + k];
+        C2 o;
+        o.x = w * z.x;
+        o.y = w * z.y;
+        W[(long long)b * Nc + k] = o;
+    }
+}
+
+// Contact values from the ball averages nbar [M][Nr] (grid layout), the arithmetic of the direct
+// contact kernel: xi_k = sum_b xi_k-coefficient_b nbar_b, g_ab = BMCSL(xi2, xi3; s_ab).  Writes
+// g_ab [M][M][N], optionally xi2, xi3 [2][N], and g_{a_q b_q} n_{b_q} of every pair q into the grid
+// fields G [npairs][Nr] (zero outside the lattice).  Row kernel over the grid.
+template <typename T, int M>
+__global__ void k_spec_contact(Grid g, int L0, int L1, long long Nr, ContactParams cp, SpecPairs sp,
+                               const T *__restrict__ npad, const T *__restrict__ nbar, T *__restrict__ gab,
+                               T *__restrict__ xi_out, T *__restrict__ G, int *err) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L0) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    if (!(x < g.nx && y < g.ny && z < g.nz)) {
+        for (int q = 0; q < sp.npairs; ++q) G[(long long)q * Nr + idx] = (T)0;
+        return;
+    }
+    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    const long long pi = pidx(g, x, y, z);
+    T xi2 = 0, xi3 = 0, nl[M];
+#pragma unroll
+    for (int b = 0; b < M; ++b) {
+        const T nb = nbar[(long long)b * Nr + idx];
+        xi2 += (T)cp.xi2c[b] * nb;
+        xi3 += (T)cp.xi3c[b] * nb;
+        nl[b] = npad[(long long)b * g.P + pi];
+    }
+    const T i1 = (T)1 / ((T)1 - xi3);
+    if (!(xi3 < (T)1)) atomicOr(err, ERR_PACKING);
+    if (xi_out) {
+        xi_out[i] = xi2;
+        xi_out[g.N + i] = xi3;
+    }
+    T gv[M][M];
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const T s = (T)cp.s_ab[a][b];
+            gv[a][b] = i1 + (T)3 * s * xi2 * i1 * i1 + (T)2 * s * s * xi2 * xi2 * i1 * i1 * i1;
+            if (!isfinite(gv[a][b])) atomicOr(err, ERR_PACKING);
+            gab[(long long)(a * M + b) * g.N + i] = gv[a][b];
+        }
     for (int q = 0; q < sp.npairs; ++q) {
-        T v = (T)0;
-        if (in) v = gab[(long long)(sp.a[q] * sp.M + sp.b[q]) * g.N + i] * npad[(long long)sp.b[q] * g.P + pi];
-        R[(long long)(sp.M + q) * Nr + idx] = v;
+        T v = 0;
+#pragma unroll
+        for (int a = 0; a < M; ++a)
+#pragma unroll
+            for (int b = 0; b < M; ++b)
+                if (sp.a[q] == a && sp.b[q] == b) v = gv[a][b] * nl[b];
+        G[(long long)q * Nr + idx] = v;
     }
 }
 
@@ -282,34 +360,8 @@ __global__ void k_spec_combine(Grid g, int L0, int L1, long long Nr, const T *__
                 Pout[((long long)q * 3 + c) * g.N + i] = R[((long long)3 * q + c) * Nr + ri];
 }
 
-// The same three kernels for M = 1 or 2 species with all M^2 pairs present, in the order q = a M + b:
-// every loop has compile-time bounds, so the sums stay in registers.
-template <typename T, int M>
-__global__ void k_spec_embed_m(Grid g, int L0, int L1, long long Nr, const T *__restrict__ npad,
-                               const T *__restrict__ gab, T *__restrict__ R) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= L0) return;
-    const int y = blockIdx.y, z = blockIdx.z;
-    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
-    T n[M], gn[M * M];
-#pragma unroll
-    for (int b = 0; b < M; ++b) n[b] = (T)0;
-#pragma unroll
-    for (int q = 0; q < M * M; ++q) gn[q] = (T)0;
-    if (x < g.nx && y < g.ny && z < g.nz) {
-        const long long pi = pidx(g, x, y, z);
-        const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
-#pragma unroll
-        for (int b = 0; b < M; ++b) n[b] = npad[(long long)b * g.P + pi];
-#pragma unroll
-        for (int q = 0; q < M * M; ++q) gn[q] = gab[(long long)q * g.N + i] * n[q % M];
-    }
-#pragma unroll
-    for (int b = 0; b < M; ++b) R[(long long)b * Nr + idx] = n[b];
-#pragma unroll
-    for (int q = 0; q < M * M; ++q) R[(long long)(M + q) * Nr + idx] = gn[q];
-}
-
+// The multiply and combine kernels for M = 1 or 2 species with all M^2 pairs present, in the order
+// q = a M + b: every loop has compile-time bounds, so the sums stay in registers.
 template <typename T, int M>
 __global__ void k_spec_multiply_m(const typename Cplx<T>::type *__restrict__ Z, const T *__restrict__ tab,
                                   typename Cplx<T>::type *__restrict__ W, long long Nc, SpecPairs sp, T scale) {
@@ -418,26 +470,57 @@ cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc
     return cudaGetLastError();
 }
 
-cudaError_t launch_spec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const void *npad,
-                              const void *gab, const SpecPairs &sp, void *R, cudaStream_t st) {
-    const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
-    if (full_pairs(sp)) {
-#define LBE_SPEC_EMBED(TT, MM) \
-    k_spec_embed_m<TT, MM><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const TT *)npad, (const TT *)gab, (TT *)R)
-        if (fp64) {
-            if (sp.M == 1) LBE_SPEC_EMBED(double, 1); else LBE_SPEC_EMBED(double, 2);
-        } else {
-            if (sp.M == 1) LBE_SPEC_EMBED(float, 1); else LBE_SPEC_EMBED(float, 2);
-        }
-#undef LBE_SPEC_EMBED
-        return cudaGetLastError();
-    }
+cudaError_t launch_spec_real(bool fp64, const void *Z, void *tab, long long Nc, cudaStream_t st) {
     if (fp64)
-        k_spec_embed<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const double *)npad, (const double *)gab, sp,
-                                                   (double *)R);
+        k_spec_real<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z, (double *)tab, Nc);
     else
-        k_spec_embed<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, (const float *)npad, (const float *)gab, sp,
-                                                  (float *)R);
+        k_spec_real<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z, (float *)tab, Nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_embed_n(bool fp64, const Grid &g, const int L[3], long long Nr, int M, const void *npad,
+                                void *R, cudaStream_t st) {
+    const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
+    if (fp64)
+        k_spec_embed_n<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, M, (const double *)npad, (double *)R);
+    else
+        k_spec_embed_n<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, M, (const float *)npad, (float *)R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_ball_mul(bool fp64, const void *Z, const void *btab, void *W, long long Nc, int M,
+                                 double scale, cudaStream_t st) {
+    if (fp64)
+        k_spec_ball_mul<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z, (const double *)btab, (double2 *)W,
+                                                            Nc, M, scale);
+    else
+        k_spec_ball_mul<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z, (const float *)btab, (float2 *)W, Nc,
+                                                           M, (float)scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spec_contact(bool fp64, const Grid &g, const int L[3], long long Nr, const ContactParams &cp,
+                                const SpecPairs &sp, const void *npad, const void *nbar, void *gab, void *xi, void *G,
+                                int *err, cudaStream_t st) {
+    const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
+#define LBE_SPEC_CONTACT(TT, MM)                                                                              \
+    k_spec_contact<TT, MM><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, cp, sp, (const TT *)npad, (const TT *)nbar, \
+                                                 (TT *)gab, (TT *)xi, (TT *)G, err)
+#define LBE_SPEC_CONTACT_M(TT)                   \
+    switch (sp.M) {                              \
+        case 1: LBE_SPEC_CONTACT(TT, 1); break;  \
+        case 2: LBE_SPEC_CONTACT(TT, 2); break;  \
+        case 3: LBE_SPEC_CONTACT(TT, 3); break;  \
+        case 4: LBE_SPEC_CONTACT(TT, 4); break;  \
+        default: return cudaErrorInvalidValue;   \
+    }
+    if (fp64) {
+        LBE_SPEC_CONTACT_M(double);
+    } else {
+        LBE_SPEC_CONTACT_M(float);
+    }
+#undef LBE_SPEC_CONTACT_M
+#undef LBE_SPEC_CONTACT
     return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ def test_methods_agree_over_fp32_channel_steps():
 def test_automatic_choice_and_errors():
     from paper_1202_3842_gb300 import lbe
     # mean shell 340 points on a grid 2.1 times the lattice: above the FP64 break-even (110 x 2.1),
-    # below FP32's (340 x 2.1)
+    # below FP32's (320 x 2.1)
     w, arr = case_channel((30, 16, 14), (4.0, 6.0), 0.2, (1.0, 1.0), 8, 6)
     assert setup_gpu(w, arr, "fp64").shell_method() == "spectral"
     assert setup_gpu(w, arr, "fp32").shell_method() == "direct"
