@@ -87,9 +87,12 @@ typedef enum { LBE_DD_TR = 0, LBE_SD_TR = 1, LBE_SD_EU = 2, LBE_DD_EU = 3 } lbe_
  *     mean shell of the pairs above about 320 points (FP32 arithmetic) or 110
  *     points (FP64, where the stencil is bound by the FP64 rate), scaled by
  *     the padded grid over the lattice; direct otherwise.
- * Both give the sums of the definition up to rounding.  The adjoint
- * (lbe_adjoint_flux_gradient) needs every pair diameter to have a direct
- * stencil. */
+ * Both give the sums of the definition up to rounding.  The discrete adjoint
+ * (lbe_adjoint_flux_gradient) transposes the shell sums with the method this
+ * call sets: the stencil (pair diameters with a compiled stencil), the
+ * spectral form (any), or under LBE_SHELL_AUTO the spectral form unless the
+ * shells are small (the stencil transpose costs about 2.6 times the forward
+ * stencil, so the rule's break-even is divided by 2.6). */
 typedef enum { LBE_SHELL_AUTO = 0, LBE_SHELL_DIRECT = 1, LBE_SHELL_SPECTRAL = 2 } lbe_shell_method;
 
 /* Optional device allocator.  alloc returns device memory of at least `bytes`

@@ -302,7 +302,8 @@ __global__ void k_adj_shell_prep(Grid g, const T *__restrict__ npad_a, const T *
     for (int c = 0; c < 3; ++c) {
         const T lc = lC_a[(long long)c * g.N + i];
         const T L = s * lc;
-        if constexpr (sizeof(T) == 4) {  // FP32: interleaved (Lambda_c, g Lambda_c), [3][P] float2 in Lpad
+        if (!Lpad) {  // the spectral transposes form Lambda themselves
+        } else if constexpr (sizeof(T) == 4) {  // FP32: interleaved (Lambda_c, g Lambda_c), [3][P] float2 in Lpad
             write_padded<float2>(g, reinterpret_cast<float2 *>(Lpad) + (long long)c * g.P, x, y, z,
                                  make_float2(L, gv * L));
         } else {

@@ -314,7 +314,7 @@ int shell_count(int S) {
 // the two break even at a mean shell of about 280 (well) to 323 (channel) points per pair in FP32,
 // scaled by the lattice over the grid, and about 100 in FP64, where the stencil is bound by the FP64
 // rate.  The constants lean to the stencil.
-bool spectral_cheaper(const lbe_ctx *c, bool f64) {
+bool spectral_cheaper(const lbe_ctx *c, bool f64, double stencil_factor = 1.0) {
     long long pts = 0;
     int Smax = 0;
     for (const auto &ps : c->pairs) {
@@ -325,61 +325,48 @@ bool spectral_cheaper(const lbe_ctx *c, bool f64) {
     const int n3[3] = {g.nx, g.ny, g.nz};
     double Nr = 1.0;
     for (int k = 0; k < 3; ++k) Nr *= g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
-    const double even = f64 ? 110.0 : 320.0;
+    const double even = (f64 ? 110.0 : 320.0) / stencil_factor;
     return spectral_shape_ok(c, Smax) && (double)pts * (double)g.N > even * (double)c->pairs.size() * Nr;
 }
 
-// Plans, buffers and shell spectra of the spectral K3 (lbe_spectral.cu) for the current pairs.
-lbe_status spectral_setup(lbe_ctx *c) {
-    const bool f64 = prec_fp64(c->prec);
-    const size_t rb = real_bytes(c);
-    const Grid &g = c->g;
+// The pairs as the spectral kernels see them (shell index into the table of distinct shells), the
+// distinct shells, and the grid: the lattice along periodic axes, at least Smax zero planes beyond it
+// along closed axes.
+void spectral_pairs(const lbe_ctx *c, SpecPairs *sp, std::vector<int> *shells, int L[3]) {
+    *sp = SpecPairs{};
+    shells->clear();
     int Smax = 0;
-    std::vector<int> shells;
-    SpecPairs sp{};
-    sp.M = c->M;
-    sp.npairs = (int)c->pairs.size();
-    for (int q = 0; q < sp.npairs; ++q) {
+    sp->M = c->M;
+    sp->npairs = (int)c->pairs.size();
+    for (int q = 0; q < sp->npairs; ++q) {
         const PairShell &ps = c->pairs[q];
         Smax = std::max(Smax, ps.S);
         int s = 0;
-        while (s < (int)shells.size() && shells[s] != ps.S) ++s;
-        if (s == (int)shells.size()) shells.push_back(ps.S);
-        sp.a[q] = ps.a;
-        sp.b[q] = ps.b;
-        sp.s[q] = s;
-        sp.half_coef[q] = 0.5 * ps.coef;
+        while (s < (int)shells->size() && (*shells)[s] != ps.S) ++s;
+        if (s == (int)shells->size()) shells->push_back(ps.S);
+        sp->a[q] = ps.a;
+        sp->b[q] = ps.b;
+        sp->s[q] = s;
+        sp->half_coef[q] = 0.5 * ps.coef;
     }
-    // the grid: the lattice along periodic axes; at least Smax zero planes beyond it along closed axes
+    const Grid &g = c->g;
     const int n3[3] = {g.nx, g.ny, g.nz};
-    int L[3];
     for (int k = 0; k < 3; ++k) L[k] = g.per[k] ? n3[k] : fft_size(n3[k] + Smax);
-    if (!spectral_shape_ok(c, Smax))
-        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: an axis of the grid is longer than 65535");
-    const int M = c->M, nfwd = M + sp.npairs, ninv = 3 * sp.npairs + 3 * M, nS = (int)shells.size();
-    spectral_destroy(c->spec);
-    c->spec = nullptr;
-    std::string why;
-    size_t ws = 0;
-    if (spectral_create(&c->spec, f64, L, M, sp.npairs, ninv, &ws, &why) != 0)
-        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: " + why);
-    const long long Nr = (long long)L[0] * L[1] * L[2], Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
-    // real fields: the densities, the pairs' g n and the ball averages, later the ninv force fields
-    TRY(dev_alloc(c, c->specR, rb * (size_t)std::max(ninv, std::max(nfwd + M, 3)) * Nr));
-    TRY(dev_alloc(c, c->specZ, 2 * rb * (size_t)std::max(nfwd, 3) * Nc));
-    TRY(dev_alloc(c, c->specW, 2 * rb * (size_t)ninv * Nc));
-    // tables: t_c of every shell [nS][3][Nc], then the ball spectrum of every species [M][Nc]
-    TRY(dev_alloc(c, c->specTab, rb * (size_t)(3 * nS + M) * Nc));
-    TRY(dev_alloc(c, c->specWork, ws));
-    if (spectral_bind(c->spec, c->specWork.p, c->stream) != 0)
-        return fail(c, LBE_ERR_CUDA, "spectral shell force: binding the cuFFT work area failed");
-    for (int k = 0; k < 3; ++k) c->specL[k] = L[k];
-    c->specNr = Nr;
-    c->specNc = Nc;
-    c->specPairs = sp;
+}
+
+// Spectra of the shell kernels, t_c = Im FFT(kappa_c) with kappa_c(-e mod L) = e_c / |e|, into tab
+// [nS][3][Nc]; with balls, then the ball spectra Re FFT(beta_b), beta_b(-d mod L) = 1 / |B_b| on the ball
+// rows of the contact kernel (even, so the spectrum is real), into tab [M][Nc] after them.  R and Z are
+// scratch of three fields; `spec` has the three-field forward plan 2.
+lbe_status spectral_tables(lbe_ctx *c, SpectralShell *spec, const int L[3], long long Nr, long long Nc,
+                           const std::vector<int> &shells, bool balls, void *tab, void *R, void *Z) {
+    const bool f64 = prec_fp64(c->prec);
+    const size_t rb = real_bytes(c);
+    const int M = c->M, nS = (int)shells.size();
+    void *const specR = R, *const specZ = Z, *const specTab = tab;
     // shell spectra t_c = Im FFT(kappa_c), kappa_c(-e mod L) = e_c / |e|; ball spectra Re FFT(beta_b),
     // beta_b(-d mod L) = 1 / |B_b| on the ball rows of the contact kernel (even, so the spectrum is real)
-    const int ntab = nS + M;
+    const int ntab = nS + (balls ? M : 0);
     std::vector<std::vector<int>> eh(ntab);
     std::vector<std::vector<double>> uh(ntab);
     std::vector<Buf> ed(ntab), ud(ntab);
@@ -414,27 +401,26 @@ lbe_status spectral_setup(lbe_ctx *c) {
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(ud[s].p, uh[s].data(), sizeof(double) * uh[s].size(), cudaMemcpyHostToDevice,
                                 c->stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(c->specR.p, 0, rb * 3 * Nr, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(specR, 0, rb * 3 * Nr, c->stream);
         if (e == cudaSuccess)
-            e = launch_spec_table(f64, c->specR.p, Nr, L, (const int *)ed[s].p, (const double *)ud[s].p, ne, c->stream);
+            e = launch_spec_table(f64, specR, Nr, L, (const int *)ed[s].p, (const double *)ud[s].p, ne, c->stream);
         if (e != cudaSuccess) {
             st = cuda_fail(c, e, "spectral shell tables");
             break;
         }
         c->launches += 1;
-        if (spectral_forward(c->spec, 2, c->specR.p, c->specZ.p) != 0) {
+        if (spectral_forward(spec, 2, specR, specZ) != 0) {
             st = fail(c, LBE_ERR_CUDA, "spectral shell tables: cuFFT forward transform failed");
             break;
         }
         if (s < nS)
-            e = launch_spec_imag(f64, c->specZ.p, (char *)c->specTab.p + rb * 3 * (size_t)s * Nc, Nc, c->stream);
+            e = launch_spec_imag(f64, specZ, (char *)specTab + rb * 3 * (size_t)s * Nc, Nc, c->stream);
         else
-            e = launch_spec_real(f64, c->specZ.p, (char *)c->specTab.p + rb * (size_t)(3 * nS + s - nS) * Nc, Nc,
+            e = launch_spec_real(f64, specZ, (char *)specTab + rb * (size_t)(3 * nS + s - nS) * Nc, Nc,
                                  c->stream);
         c->launches += 1;
         if (e != cudaSuccess) st = cuda_fail(c, e, "spectral shell tables");
     }
-    c->specNS = nS;
     cudaError_t e = cudaStreamSynchronize(c->stream);  // the host lists must outlive their copies
     for (int s = 0; s < ntab; ++s) {
         dev_free(c, ed[s]);
@@ -443,6 +429,43 @@ lbe_status spectral_setup(lbe_ctx *c) {
     if (st != LBE_OK) return st;
     if (e != cudaSuccess) return cuda_fail(c, e, "spectral shell tables");
     return LBE_OK;
+}
+
+// Plans, buffers and shell and ball spectra of the spectral K2 + K3 (lbe_spectral.cu) for the current pairs.
+lbe_status spectral_setup(lbe_ctx *c) {
+    const bool f64 = prec_fp64(c->prec);
+    const size_t rb = real_bytes(c);
+    SpecPairs sp;
+    std::vector<int> shells;
+    int L[3];
+    spectral_pairs(c, &sp, &shells, L);
+    int Smax = 0;
+    for (int S : shells) Smax = std::max(Smax, S);
+    if (!spectral_shape_ok(c, Smax))
+        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: an axis of the grid is longer than 65535");
+    const int M = c->M, nfwd = M + sp.npairs, ninv = 3 * sp.npairs + 3 * M, nS = (int)shells.size();
+    spectral_destroy(c->spec);
+    c->spec = nullptr;
+    std::string why;
+    size_t ws = 0;
+    if (spectral_create(&c->spec, f64, L, M, sp.npairs, ninv, &ws, &why) != 0)
+        return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell force: " + why);
+    const long long Nr = (long long)L[0] * L[1] * L[2], Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
+    // real fields: the densities, the pairs' g n and the ball averages, later the ninv force fields
+    TRY(dev_alloc(c, c->specR, rb * (size_t)std::max(ninv, std::max(nfwd + M, 3)) * Nr));
+    TRY(dev_alloc(c, c->specZ, 2 * rb * (size_t)std::max(nfwd, 3) * Nc));
+    TRY(dev_alloc(c, c->specW, 2 * rb * (size_t)ninv * Nc));
+    // tables: t_c of every shell [nS][3][Nc], then the ball spectrum of every species [M][Nc]
+    TRY(dev_alloc(c, c->specTab, rb * (size_t)(3 * nS + M) * Nc));
+    TRY(dev_alloc(c, c->specWork, ws));
+    if (spectral_bind(c->spec, c->specWork.p, c->stream) != 0)
+        return fail(c, LBE_ERR_CUDA, "spectral shell force: binding the cuFFT work area failed");
+    for (int k = 0; k < 3; ++k) c->specL[k] = L[k];
+    c->specNr = Nr;
+    c->specNc = Nc;
+    c->specPairs = sp;
+    c->specNS = nS;
+    return spectral_tables(c, c->spec, L, Nr, Nc, shells, true, c->specTab.p, c->specR.p, c->specZ.p);
 }
 
 // K2 and K3 in spectral form: g_ab [M][M][N] (xi2, xi3 into xibase for the adjoint) and C [M][3][N]
@@ -1436,10 +1459,30 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     if (c->cfg.scheme != LBE_DD_TR) return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint is that of the DD-TR scheme");
     TRY(prepare(c));
     const bool f64 = prec_fp64(c->prec);
-    for (const auto &ps : c->pairs)
-        if (!shell_supported(f64, ps.S))
+    // K3 transposed: the stencil tiles, or the spectral form (the same sums as correlations with the
+    // forward kernel).  The stencil transposes read a 2-vector per component and shell point, about 2.6
+    // times the forward stencil's shared-memory work (measured on GB300), so the automatic choice
+    // weighs the stencil side by that factor.
+    bool adj_direct_ok = true;
+    int adj_smax = 0;
+    for (const auto &ps : c->pairs) {
+        adj_direct_ok = adj_direct_ok && shell_supported(f64, ps.S);
+        adj_smax = std::max(adj_smax, ps.S);
+    }
+    bool adj_spectral = false;
+    if (!c->pairs.empty()) {
+        std::string why;
+        const bool can_spectral = spectral_available(&why) && spectral_shape_ok(c, adj_smax);
+        if (c->shell_method == LBE_SHELL_SPECTRAL)
+            adj_spectral = true;
+        else if (c->shell_method == LBE_SHELL_AUTO)
+            adj_spectral = can_spectral && (!adj_direct_ok || spectral_cheaper(c, f64, 2.6));
+        if (adj_spectral && !can_spectral)
+            return fail(c, LBE_ERR_UNSUPPORTED, "the spectral shell transpose is not available: " + why);
+        if (!adj_spectral && !adj_direct_ok)
             return fail(c, LBE_ERR_UNSUPPORTED, "the shell transpose has no compiled stencil for pair diameter " +
-                                                    std::to_string(ps.S));
+                                                    std::to_string(adj_smax));
+    }
     const size_t rb = real_bytes(c);
     const long long N = c->g.N, P = c->g.P;
     const int M = c->M;
@@ -1458,12 +1501,17 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                  slot_bytes = sl_P + rb * 3 * (size_t)std::max(npairs, 1) * N;
     std::vector<Buf> ck(nseg), seg(kseg), slot(kseg);
     Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, lmom, outA, red;
+    Buf aR, aZ, aW, aTab, aWork;  // the spectral transpose's grid fields, spectra, tables, cuFFT work area
+    SpectralShell *aspec = nullptr;
     auto release = [&]() {
         for (auto &b : ck) dev_free(c, b);
         for (auto &b : seg) dev_free(c, b);
         for (auto &b : slot) dev_free(c, b);
         Buf *all[] = {&lYf[0], &lYf[1], &lYg[0], &lYg[1], &lnd[0], &lnd[1], &lC, &lF, &lg, &Lpad, &gLpad,
-                      &lnbar, &lmom, &outA, &red};
+                      &lnbar, &lmom, &outA, &red, &aR, &aZ, &aW, &aTab, &aWork};
+        cudaStreamSynchronize(c->stream);
+        spectral_destroy(aspec);
+        aspec = nullptr;
         for (Buf *b : all) dev_free(c, *b);
     };
     auto alloc = [&](Buf &b, size_t bytes, bool zero) -> lbe_status {
@@ -1492,8 +1540,10 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     ATRY(alloc(lC, rb * M * 3 * N, true));
     ATRY(alloc(lF, rb * M * 3 * N, true));
     ATRY(alloc(lg, rb * M * M * N, true));
-    ATRY(alloc(Lpad, (f64 ? rb : 2 * rb) * 3 * P, true));  // FP32: interleaved (Lambda_c, g Lambda_c)
-    if (f64) ATRY(alloc(gLpad, rb * 3 * P, true));
+    if (!adj_spectral) {
+        ATRY(alloc(Lpad, (f64 ? rb : 2 * rb) * 3 * P, true));  // FP32: interleaved (Lambda_c, g Lambda_c)
+        if (f64) ATRY(alloc(gLpad, rb * 3 * P, true));
+    }
     ATRY(alloc(lnbar, rb * M * P, true));
     ATRY(alloc(lmom, rb * M * 5 * N, false));
     ATRY(alloc(outA, 8 * N, false));
@@ -1506,9 +1556,39 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
         contact_box(f64, M, c->RB, &bx, &by);
         for (int b = 0; b < M; ++b) ATRY(make_map(c, &ballmaps[b], (char *)lnbar.p + rb * b * P, bx, by));
     }
+    // the spectral transpose: grid fields lambda [M][3] and g lambda [npairs][3], spectra TQ [npairs]
+    // and TP [M] (lbe_spectral.cu)
+    SpecPairs asp{};
+    int aL[3] = {0, 0, 0};
+    long long aNr = 0, aNc = 0;
+    if (adj_spectral) {
+        std::vector<int> shells;
+        spectral_pairs(c, &asp, &shells, aL);
+        const int nf = 3 * M + 3 * npairs, ni = npairs + M;
+        const int batch[3] = {nf, ni, 3};
+        const bool fwd[3] = {true, false, true};
+        std::string why;
+        size_t ws = 0;
+        if (spectral_create_plans(&aspec, f64, aL, 3, batch, fwd, &ws, &why) != 0) {
+            release();
+            return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell transpose: " + why);
+        }
+        aNr = (long long)aL[0] * aL[1] * aL[2];
+        aNc = (long long)(aL[0] / 2 + 1) * aL[1] * aL[2];
+        ATRY(alloc(aR, rb * (size_t)std::max(nf, 3) * aNr, false));
+        ATRY(alloc(aZ, 2 * rb * (size_t)std::max(nf, 3) * aNc, false));
+        ATRY(alloc(aW, 2 * rb * (size_t)ni * aNc, false));
+        ATRY(alloc(aTab, rb * 3 * shells.size() * aNc, false));
+        ATRY(alloc(aWork, ws, false));
+        if (spectral_bind(aspec, aWork.p, c->stream) != 0) {
+            release();
+            return fail(c, LBE_ERR_CUDA, "spectral shell transpose: binding the cuFFT work area failed");
+        }
+        ATRY(spectral_tables(c, aspec, aL, aNr, aNc, shells, false, aTab.p, aR.p, aZ.p));
+    }
     // tensor maps of the padded Lambda_c and (g Lambda)_c with the box of each pair's shell
     std::vector<CUtensorMap> mapL(3 * npairs), mapgL(3 * npairs);
-    for (int q = 0; q < npairs; ++q) {
+    for (int q = 0; q < npairs && !adj_spectral; ++q) {
         int bx = 0, by = 0;
         if (f64) {
             adj_shell_box(true, c->pairs[q].S, &bx, &by);
@@ -1591,14 +1671,15 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                 L.lC_a = (const char *)lC.p + rb * 3 * ps.a * N;
                 L.P = sl + sl_P + rb * 3 * q * N;
                 L.C_a = sl + sl_C + rb * 3 * ps.a * N;
-                L.Lpad = Lpad.p;
-                L.gLpad = gLpad.p;
+                L.Lpad = adj_spectral ? nullptr : Lpad.p;  // the spectral transpose forms Lambda itself
+                L.gLpad = adj_spectral ? nullptr : gLpad.p;
                 L.coef = ps.coef;
                 L.own = own[ps.a];
                 own[ps.a] = 0;
                 L.ln_a = (char *)lnd[1 - cl].p + rb * ps.a * N;
                 L.lg = (char *)lg.p + rb * (ps.a * M + ps.b) * N;
                 LAUNCH(launch_adj_shell_prep(f64, c->g, L, c->stream), "adjoint shell prep");
+                if (adj_spectral) continue;
                 AdjShellTile LT{};
                 LT.grid = &c->g;
                 LT.maps_L = &mapL[3 * q];
@@ -1610,6 +1691,24 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                 LT.err = (int *)c->err.p;
                 LAUNCH(launch_adj_shell_tile(f64, ps.S, LT, c->stream), "adjoint shell");
                 c->launches += 2;  // one launch per component
+            }
+            if (npairs && adj_spectral) {
+                // the shell sums of the transpose for every pair at once (lbe_spectral.cu)
+                LAUNCH(launch_adjspec_embed(f64, c->g, aL, aNr, asp, sl + sl_npad, lC.p, sl + sl_gab, aR.p, c->stream),
+                       "adjoint spectral embed");
+                if (spectral_forward(aspec, 0, aR.p, aZ.p) != 0) {
+                    release();
+                    return fail(c, LBE_ERR_CUDA, "spectral shell transpose: cuFFT forward transform failed");
+                }
+                LAUNCH(launch_adjspec_multiply(f64, aZ.p, aTab.p, aW.p, aNc, asp, 1.0 / (double)aNr, c->stream),
+                       "adjoint spectral multiply");
+                if (spectral_inverse(aspec, 1, aW.p, aR.p) != 0) {
+                    release();
+                    return fail(c, LBE_ERR_CUDA, "spectral shell transpose: cuFFT inverse transform failed");
+                }
+                LAUNCH(launch_adjspec_combine(f64, c->g, aL, aNr, asp, aR.p, sl + sl_npad, sl + sl_gab,
+                                              lnd[1 - cl].p, lg.p, c->stream),
+                       "adjoint spectral combine");
             }
             if (npairs) {
                 LAUNCH(launch_adj_contact_prep(f64, c->g, c->cparams, c->brows, sl + sl_xi, lg.p, lnbar.p, c->stream),

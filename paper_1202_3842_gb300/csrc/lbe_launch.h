@@ -219,6 +219,9 @@ bool spectral_available(std::string *why);
 // averages (4).  Returns 0, or -1 with the reason in *why.
 int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int npairs, int ninv, size_t *work_bytes,
                     std::string *why);
+// The same with any plan list: plan k transforms batch[k] fields, forward (real to half spectrum) or not.
+int spectral_create_plans(SpectralShell **out, bool fp64, const int L[3], int nplans, const int *batch,
+                          const bool *forward, size_t *work_bytes, std::string *why);
 void spectral_destroy(SpectralShell *s);
 int spectral_bind(SpectralShell *s, void *work, cudaStream_t st);
 int spectral_forward(SpectralShell *s, int which /* 0, 2 or 3 */, void *R, void *Z);
@@ -227,6 +230,14 @@ cudaError_t launch_spec_table(bool fp64, void *R3, long long Nr, const int L[3],
                               cudaStream_t st);
 cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc, cudaStream_t st);
 cudaError_t launch_spec_real(bool fp64, const void *Z, void *tab, long long Nc, cudaStream_t st);
+// K3 transposed in spectral form (discrete adjoint)
+cudaError_t launch_adjspec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const SpecPairs &sp,
+                                 const void *npad, const void *lC, const void *gab, void *R, cudaStream_t st);
+cudaError_t launch_adjspec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc,
+                                    const SpecPairs &sp, double scale, cudaStream_t st);
+cudaError_t launch_adjspec_combine(bool fp64, const Grid &g, const int L[3], long long Nr, const SpecPairs &sp,
+                                   const void *R, const void *npad, const void *gab, void *ln, void *lg,
+                                   cudaStream_t st);
 cudaError_t launch_spec_embed_n(bool fp64, const Grid &g, const int L[3], long long Nr, int M, const void *npad,
                                 void *R, cudaStream_t st);
 cudaError_t launch_spec_ball_mul(bool fp64, const void *Z, const void *btab, void *W, long long Nc, int M,

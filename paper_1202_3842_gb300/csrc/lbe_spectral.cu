@@ -117,7 +117,15 @@ void spectral_destroy(SpectralShell *s) {
 
 int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int npairs, int ninv, size_t *work_bytes,
                     std::string *why) {
+    const int batch[SpectralShell::NPLAN] = {M, ninv, 3, npairs, M};
+    const bool forward[SpectralShell::NPLAN] = {true, false, true, true, false};
+    return spectral_create_plans(out, fp64, L, SpectralShell::NPLAN, batch, forward, work_bytes, why);
+}
+
+int spectral_create_plans(SpectralShell **out, bool fp64, const int L[3], int nplans, const int *batch,
+                          const bool *forward, size_t *work_bytes, std::string *why) {
     *out = nullptr;
+    if (nplans < 1 || nplans > SpectralShell::NPLAN) return -1;
     const CufftApi *api = cufft_api(why);
     if (!api) return -1;
     SpectralShell *s = new SpectralShell();
@@ -127,11 +135,9 @@ int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int n
     s->Nr = (long long)L[0] * L[1] * L[2];
     s->Nc = (long long)(L[0] / 2 + 1) * L[1] * L[2];
     int n[3] = {L[2], L[1], L[0]};  // row-major: x is the fastest (and the halved) dimension
-    const int batch[SpectralShell::NPLAN] = {M, ninv, 3, npairs, M};
     const cufftType fwd = fp64 ? CUFFT_D2Z : CUFFT_R2C, inv = fp64 ? CUFFT_Z2D : CUFFT_C2R;
-    const cufftType type[SpectralShell::NPLAN] = {fwd, inv, fwd, fwd, inv};
     size_t wmax = 0;
-    for (int k = 0; k < SpectralShell::NPLAN; ++k) {
+    for (int k = 0; k < nplans; ++k) {
         cufftResult r = api->create(&s->plan[k]);
         if (r != CUFFT_SUCCESS) {
             if (why) *why = "cufftCreate failed (" + std::to_string((int)r) + ")";
@@ -141,7 +147,7 @@ int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int n
         s->made[k] = true;
         api->set_auto(s->plan[k], 0);
         size_t ws = 0;
-        r = api->make_many(s->plan[k], 3, n, nullptr, 1, 0, nullptr, 1, 0, type[k], batch[k], &ws);
+        r = api->make_many(s->plan[k], 3, n, nullptr, 1, 0, nullptr, 1, 0, forward[k] ? fwd : inv, batch[k], &ws);
         if (r != CUFFT_SUCCESS) {
             if (why) *why = "cufftMakePlanMany failed (" + std::to_string((int)r) + ")";
             spectral_destroy(s);
@@ -156,6 +162,7 @@ int spectral_create(SpectralShell **out, bool fp64, const int L[3], int M, int n
 
 int spectral_bind(SpectralShell *s, void *work, cudaStream_t st) {
     for (int k = 0; k < SpectralShell::NPLAN; ++k) {
+        if (!s->made[k]) continue;
         if (s->api->set_work(s->plan[k], work) != CUFFT_SUCCESS) return -1;
         if (s->api->set_stream(s->plan[k], st) != CUFFT_SUCCESS) return -1;
     }
@@ -438,6 +445,104 @@ __global__ void k_spec_combine_m(Grid g, int L0, int L1, long long Nr, const T *
             for (int c = 0; c < 3; ++c) Pout[((long long)q * 3 + c) * g.N + i] = P[q][c];
 }
 
+// ---------------------------------------------------------------------------
+// K3 transposed in spectral form (discrete adjoint).  For the pair q = (a, b) with Lambda_q = coef_q
+// lambda_a, lambda_a = n_a lC^a / 2 (lC^a the adjoint of C^a), the shell sums of the transpose,
+//   TQ_q(s) = sum_e e^ . Lambda_q(s + e),   TP_q(s) = sum_e e^ . (g_q Lambda_q)(s + e),
+// are correlations with the forward kernel, so their spectra are i t_c times those of the fields.
+// lambda_a does not depend on b: its transform serves every pair of species a.  The TP of the pairs
+// of one species b are summed in spectral space (they enter only ln_b):
+//   ln_b(s) -= TP_b(s) + sum_{q: b_q = b} g_q(s) TQ_q(s),   lg_q(s) -= n_b(s) TQ_q(s).
+// Grid fields: lambda [M][3], then g lambda [npairs][3] (real); spectra TQ [npairs], TP [M].
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_adjspec_embed(Grid g, int L0, int L1, long long Nr, SpecPairs sp, const T *__restrict__ npad,
+                                const T *__restrict__ lC, const T *__restrict__ gab, T *__restrict__ R) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= L0) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long idx = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    const bool in = x < g.nx && y < g.ny && z < g.nz;
+    const long long i = in ? (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z) : 0;
+    const long long pi = in ? pidx(g, x, y, z) : 0;
+    for (int a = 0; a < sp.M; ++a) {
+        const T h = in ? (T)0.5 * npad[(long long)a * g.P + pi] : (T)0;
+        for (int c = 0; c < 3; ++c)
+            R[((long long)a * 3 + c) * Nr + idx] = in ? h * lC[((long long)a * 3 + c) * g.N + i] : (T)0;
+    }
+    for (int q = 0; q < sp.npairs; ++q) {
+        const int a = sp.a[q];
+        const T gh = in ? gab[(long long)(a * sp.M + sp.b[q]) * g.N + i] * (T)0.5 * npad[(long long)a * g.P + pi]
+                        : (T)0;
+        for (int c = 0; c < 3; ++c)
+            R[((long long)(3 * sp.M + 3 * q + c)) * Nr + idx] = in ? gh * lC[((long long)a * 3 + c) * g.N + i] : (T)0;
+    }
+}
+
+// W[q] = coef_q sum_c i t_{s_q,c} lambda^_{a_q,c};  W[npairs + b] = sum_{q: b_q = b} coef_q sum_c i t (g lambda)^_{q,c}
+template <typename T>
+__global__ void k_adjspec_multiply(const typename Cplx<T>::type *__restrict__ Z, const T *__restrict__ tab,
+                                   typename Cplx<T>::type *__restrict__ W, long long Nc, SpecPairs sp, T scale) {
+    using C2 = typename Cplx<T>::type;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Nc) return;
+    for (int q = 0; q < sp.npairs; ++q) {
+        T re = 0, im = 0;
+        for (int c = 0; c < 3; ++c) {
+            const T t = tab[((long long)sp.s[q] * 3 + c) * Nc + k];
+            const C2 l = Z[((long long)sp.a[q] * 3 + c) * Nc + k];
+            re -= t * l.y;
+            im += t * l.x;
+        }
+        const T w = (T)(2.0 * sp.half_coef[q]) * scale;
+        C2 o;
+        o.x = w * re;
+        o.y = w * im;
+        W[(long long)q * Nc + k] = o;
+    }
+    for (int b = 0; b < sp.M; ++b) {
+        T re = 0, im = 0;
+        for (int q = 0; q < sp.npairs; ++q) {
+            if (sp.b[q] != b) continue;
+            const T w = (T)(2.0 * sp.half_coef[q]);
+            for (int c = 0; c < 3; ++c) {
+                const T t = w * tab[((long long)sp.s[q] * 3 + c) * Nc + k];
+                const C2 l = Z[((long long)(3 * sp.M + 3 * q + c)) * Nc + k];
+                re -= t * l.y;
+                im += t * l.x;
+            }
+        }
+        C2 o;
+        o.x = scale * re;
+        o.y = scale * im;
+        W[(long long)(sp.npairs + b) * Nc + k] = o;
+    }
+}
+
+// ln [M][N], lg [M][M][N] of the lattice; R holds TQ [npairs] then TP [M] on the grid
+template <typename T>
+__global__ void k_adjspec_combine(Grid g, int L0, int L1, long long Nr, SpecPairs sp, const T *__restrict__ R,
+                                  const T *__restrict__ npad, const T *__restrict__ gab, T *__restrict__ ln,
+                                  T *__restrict__ lg) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const long long i = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+    const long long ri = (long long)x + (long long)L0 * ((long long)y + (long long)L1 * z);
+    const long long pi = pidx(g, x, y, z);
+    for (int b = 0; b < sp.M; ++b) {
+        T d = R[(long long)(sp.npairs + b) * Nr + ri];
+        for (int q = 0; q < sp.npairs; ++q) {
+            if (sp.b[q] != b) continue;
+            const long long gi = (long long)(sp.a[q] * sp.M + b) * g.N + i;
+            const T tq = R[(long long)q * Nr + ri];
+            d += gab[gi] * tq;
+            lg[gi] -= npad[(long long)b * g.P + pi] * tq;
+        }
+        ln[(long long)b * g.N + i] -= d;
+    }
+}
+
 // all M^2 pairs present in the order a M + b, M = 1 or 2
 bool full_pairs(const SpecPairs &sp) {
     if (sp.M > 2 || sp.npairs != sp.M * sp.M) return false;
@@ -467,6 +572,43 @@ cudaError_t launch_spec_imag(bool fp64, const void *Z3, void *tab3, long long Nc
         k_spec_imag<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z3, (double *)tab3, Nc);
     else
         k_spec_imag<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z3, (float *)tab3, Nc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjspec_embed(bool fp64, const Grid &g, const int L[3], long long Nr, const SpecPairs &sp,
+                                 const void *npad, const void *lC, const void *gab, void *R, cudaStream_t st) {
+    const dim3 grid((unsigned)((L[0] + RNT - 1) / RNT), (unsigned)L[1], (unsigned)L[2]);
+    if (fp64)
+        k_adjspec_embed<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, sp, (const double *)npad,
+                                                      (const double *)lC, (const double *)gab, (double *)R);
+    else
+        k_adjspec_embed<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, sp, (const float *)npad, (const float *)lC,
+                                                     (const float *)gab, (float *)R);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjspec_multiply(bool fp64, const void *Z, const void *tab, void *W, long long Nc,
+                                    const SpecPairs &sp, double scale, cudaStream_t st) {
+    if (fp64)
+        k_adjspec_multiply<double><<<blocks(Nc), SNT, 0, st>>>((const double2 *)Z, (const double *)tab,
+                                                               (double2 *)W, Nc, sp, scale);
+    else
+        k_adjspec_multiply<float><<<blocks(Nc), SNT, 0, st>>>((const float2 *)Z, (const float *)tab, (float2 *)W,
+                                                              Nc, sp, (float)scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjspec_combine(bool fp64, const Grid &g, const int L[3], long long Nr, const SpecPairs &sp,
+                                   const void *R, const void *npad, const void *gab, void *ln, void *lg,
+                                   cudaStream_t st) {
+    const dim3 grid((unsigned)((g.nx + RNT - 1) / RNT), (unsigned)g.ny, (unsigned)g.nz);
+    if (fp64)
+        k_adjspec_combine<double><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, sp, (const double *)R,
+                                                        (const double *)npad, (const double *)gab, (double *)ln,
+                                                        (double *)lg);
+    else
+        k_adjspec_combine<float><<<grid, RNT, 0, st>>>(g, L[0], L[1], Nr, sp, (const float *)R, (const float *)npad,
+                                                       (const float *)gab, (float *)ln, (float *)lg);
     return cudaGetLastError();
 }
 
