@@ -92,6 +92,12 @@ struct lbe_ctx {
     int specNS = 0;  // shells with a spectrum; the ball spectra follow them in specTab
     SpecPairs specPairs{};
     Buf specR, specZ, specW, specTab, specWork;
+    // the discrete adjoint's spectral shell transpose, kept between calls until the pairs change
+    SpectralShell *aspec = nullptr;
+    int aL[3] = {0, 0, 0};
+    long long aNr = 0, aNc = 0;
+    SpecPairs asp{};
+    Buf aR, aZ, aW, aTab, aWork;
 
     long long steps = 0;
     long long flux_count = 0;
@@ -621,6 +627,8 @@ lbe_status prepare(lbe_ctx *c) {
             for (int b = 0; b < c->M; ++b)
                 TRY(make_map(c, &c->contact_maps[b], (char *)c->npad.p + rb * b * g.P, bx, by));
         }
+        spectral_destroy(c->aspec);  // the adjoint's transpose plans and tables follow the pairs
+        c->aspec = nullptr;
         if (c->spectral) TRY(spectral_setup(c));
         c->fields_dirty = false;
     }
@@ -902,9 +910,12 @@ void lbe_destroy(lbe_ctx *c) {
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
                   &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec,
-                  &c->specR, &c->specZ, &c->specW, &c->specTab, &c->specWork};
+                  &c->specR, &c->specZ, &c->specW, &c->specTab, &c->specWork,
+                  &c->aR, &c->aZ, &c->aW, &c->aTab, &c->aWork};
     spectral_destroy(c->spec);
     c->spec = nullptr;
+    spectral_destroy(c->aspec);
+    c->aspec = nullptr;
     for (Buf *b : all) dev_free(c, *b);
     cudaStreamSynchronize(c->stream);
     delete c;
@@ -1501,17 +1512,12 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                  slot_bytes = sl_P + rb * 3 * (size_t)std::max(npairs, 1) * N;
     std::vector<Buf> ck(nseg), seg(kseg), slot(kseg);
     Buf lYf[2], lYg[2], lnd[2], lC, lF, lg, Lpad, gLpad, lnbar, lmom, outA, red;
-    Buf aR, aZ, aW, aTab, aWork;  // the spectral transpose's grid fields, spectra, tables, cuFFT work area
-    SpectralShell *aspec = nullptr;
     auto release = [&]() {
         for (auto &b : ck) dev_free(c, b);
         for (auto &b : seg) dev_free(c, b);
         for (auto &b : slot) dev_free(c, b);
         Buf *all[] = {&lYf[0], &lYf[1], &lYg[0], &lYg[1], &lnd[0], &lnd[1], &lC, &lF, &lg, &Lpad, &gLpad,
-                      &lnbar, &lmom, &outA, &red, &aR, &aZ, &aW, &aTab, &aWork};
-        cudaStreamSynchronize(c->stream);
-        spectral_destroy(aspec);
-        aspec = nullptr;
+                      &lnbar, &lmom, &outA, &red};
         for (Buf *b : all) dev_free(c, *b);
     };
     auto alloc = [&](Buf &b, size_t bytes, bool zero) -> lbe_status {
@@ -1557,35 +1563,45 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
         for (int b = 0; b < M; ++b) ATRY(make_map(c, &ballmaps[b], (char *)lnbar.p + rb * b * P, bx, by));
     }
     // the spectral transpose: grid fields lambda [M][3] and g lambda [npairs][3], spectra TQ [npairs]
-    // and TP [M] (lbe_spectral.cu)
-    SpecPairs asp{};
-    int aL[3] = {0, 0, 0};
-    long long aNr = 0, aNc = 0;
-    if (adj_spectral) {
+    // and TP [M] (lbe_spectral.cu); plans, buffers and shell spectra stay in the context
+    if (adj_spectral && !c->aspec) {
         std::vector<int> shells;
-        spectral_pairs(c, &asp, &shells, aL);
+        spectral_pairs(c, &c->asp, &shells, c->aL);
         const int nf = 3 * M + 3 * npairs, ni = npairs + M;
         const int batch[3] = {nf, ni, 3};
         const bool fwd[3] = {true, false, true};
         std::string why;
         size_t ws = 0;
-        if (spectral_create_plans(&aspec, f64, aL, 3, batch, fwd, &ws, &why) != 0) {
+        SpectralShell *sp_new = nullptr;
+        if (spectral_create_plans(&sp_new, f64, c->aL, 3, batch, fwd, &ws, &why) != 0) {
             release();
             return fail(c, LBE_ERR_UNSUPPORTED, "spectral shell transpose: " + why);
         }
-        aNr = (long long)aL[0] * aL[1] * aL[2];
-        aNc = (long long)(aL[0] / 2 + 1) * aL[1] * aL[2];
-        ATRY(alloc(aR, rb * (size_t)std::max(nf, 3) * aNr, false));
-        ATRY(alloc(aZ, 2 * rb * (size_t)std::max(nf, 3) * aNc, false));
-        ATRY(alloc(aW, 2 * rb * (size_t)ni * aNc, false));
-        ATRY(alloc(aTab, rb * 3 * shells.size() * aNc, false));
-        ATRY(alloc(aWork, ws, false));
-        if (spectral_bind(aspec, aWork.p, c->stream) != 0) {
+        c->aspec = sp_new;
+        c->aNr = (long long)c->aL[0] * c->aL[1] * c->aL[2];
+        c->aNc = (long long)(c->aL[0] / 2 + 1) * c->aL[1] * c->aL[2];
+        lbe_status st = LBE_OK;
+        if (st == LBE_OK) st = dev_alloc(c, c->aR, rb * (size_t)std::max(nf, 3) * c->aNr);
+        if (st == LBE_OK) st = dev_alloc(c, c->aZ, 2 * rb * (size_t)std::max(nf, 3) * c->aNc);
+        if (st == LBE_OK) st = dev_alloc(c, c->aW, 2 * rb * (size_t)ni * c->aNc);
+        if (st == LBE_OK) st = dev_alloc(c, c->aTab, rb * 3 * shells.size() * c->aNc);
+        if (st == LBE_OK) st = dev_alloc(c, c->aWork, ws);
+        if (st == LBE_OK && spectral_bind(c->aspec, c->aWork.p, c->stream) != 0)
+            st = fail(c, LBE_ERR_CUDA, "spectral shell transpose: binding the cuFFT work area failed");
+        if (st == LBE_OK) st = spectral_tables(c, c->aspec, c->aL, c->aNr, c->aNc, shells, false, c->aTab.p,
+                                               c->aR.p, c->aZ.p);
+        if (st != LBE_OK) {
+            spectral_destroy(c->aspec);
+            c->aspec = nullptr;
             release();
-            return fail(c, LBE_ERR_CUDA, "spectral shell transpose: binding the cuFFT work area failed");
+            return st;
         }
-        ATRY(spectral_tables(c, aspec, aL, aNr, aNc, shells, false, aTab.p, aR.p, aZ.p));
     }
+    SpectralShell *aspec = c->aspec;
+    const int *aL = c->aL;
+    const long long aNr = c->aNr, aNc = c->aNc;
+    const SpecPairs &asp = c->asp;
+    Buf &aR = c->aR, &aZ = c->aZ, &aW = c->aW, &aTab = c->aTab;
     // tensor maps of the padded Lambda_c and (g Lambda)_c with the box of each pair's shell
     std::vector<CUtensorMap> mapL(3 * npairs), mapgL(3 * npairs);
     for (int q = 0; q < npairs && !adj_spectral; ++q) {

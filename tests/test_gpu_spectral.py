@@ -101,4 +101,4 @@ def test_automatic_choice_and_errors():
     g = setup_gpu(w9, a9, "fp32")
     Phi, dA, dG = g.adjoint_flux_gradient(2, 1, 0, 10)
     assert np.isfinite(Phi) and np.isfinite(dA).all() and np.isfinite(dG).all()
-    assert np.abs(dA).max() > 0
+    assert abs(dG[0]) > 0  # the flux responds to the body force (no wall potential here, so dA = 0)
