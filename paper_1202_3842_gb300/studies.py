@@ -13,6 +13,8 @@ numbers; ``python -m paper_1202_3842_gb300.studies <study> [--quick]`` prints on
   residual current, for the trapezoidal and the Euler integrator, against the well size (Sec. "Ideal
   fluid in a potential well").
 - ``divergence``: max and mean |div u| in the bottleneck channel after a long run, per scheme.
+- ``init``: the transient of the spurious current from the rest state and from the quasi-pressure
+  state of the second distribution.
 
 Scheme names: ``dd_tr`` (the method, printed moment recovery), ``dd_tr_c`` (DD-TR with the
 map-consistent recovery), ``sd_tr``, ``sd_eu``, ``dd_eu``.
@@ -209,6 +211,27 @@ def divergence(schemes=("dd_tr", "sd_tr", "sd_eu", "dd_eu"), shape=(128, 32, 32)
     return out
 
 
+def init(xis=(6, 12), sigma=4.0, eta=0.2, steps=2000, prec="fp64", schemes=("dd_tr",)):
+    """The transient from the two initial states of the second distribution: Pi(0) = n(0) (the default) and
+    the quasi-pressure Pi = n - beta * path integral of C^mf + n F (Sec. "Stabilization").  Cosine well of
+    size xi in a periodic (4 xi)^3 box, hard spheres at packing eta, uniform initial density; returns
+    {scheme: {xi: {"rest": history, "quasipressure": history}}} of max|u|/v_T every 100 steps."""
+    out = {}
+    for s in schemes:
+        out[s] = {}
+        for xi in xis:
+            res = {}
+            for start in ("rest", "quasipressure"):
+                sim, _, n0 = _well_sim(s, 4 * xi, xi, [sigma], eta, prec)
+                if start == "quasipressure":
+                    sim.init_density_quasipressure(np.full((1, (4 * xi) ** 3), n0))
+                ok, hist = _run_current(sim, steps, chunk=100)
+                sim.close()
+                res[start] = hist if ok else {"error": hist}
+            out[s][int(xi)] = res
+    return out
+
+
 # Reduced sizes for a quick look (a few seconds each on one GPU).
 QUICK = {
     "spurious": dict(xis=(6,), steps=1000),
@@ -216,9 +239,10 @@ QUICK = {
     "stability": dict(etas=(0.25, 0.29), steps=500),
     "ideal_gas": dict(xis=(4, 6), steps_per_L2=3),
     "divergence": dict(shape=(64, 32, 32), length=32, steps=1000),
+    "init": dict(xis=(6,), steps=500),
 }
 STUDIES = dict(spurious=spurious, mixture=mixture, stability=stability, ideal_gas=ideal_gas,
-               divergence=divergence)
+               divergence=divergence, init=init)
 
 
 def main(argv=None):
