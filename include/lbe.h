@@ -110,7 +110,10 @@ typedef struct {
     int nspecies;             /* M, 1..4                                         */
     lbe_precision precision;
     lbe_scheme scheme;        /* LBE_DD_TR, or an ablation (see lbe_scheme)      */
-    int enable_visc;          /* C^{alpha,visc} (Appendix): must be 0             */
+    int enable_visc;          /* 1: add the viscous Enskog force C^{alpha,visc}
+                                 (Appendix) of the tilde velocities J~/n, where
+                                 the scheme adds n F (moment recovery, S_f, S_g);
+                                 LBE_DD_TR only, no discrete adjoint.  0: off  */
     int consistent_moments;   /* 0 (default): moments as printed in Sec. "Hard
                                  sphere fluid mixture": J = J~ + (C^mf + nF)/2,
                                  Pi = Pi~ - C^mf.u^alpha/2.  1: the map

@@ -46,6 +46,10 @@ def lib():
         L.or_shell_force.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_u8_p, ctypes.c_int, _c_dbl_p,
                                                           _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.or_force_field.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.or_visc_force.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_u8_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
+                                                         _c_dbl_p, _c_dbl_p, _c_dbl_p]
+        L.or_set_visc.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.or_set_visc.restype = ctypes.c_int
         L.or_quasipressure.argtypes = [ctypes.c_int] * 3 + [_c_int_p, _c_u8_p, ctypes.c_int, _c_dbl_p, _c_dbl_p,
                                                             _c_dbl_p, _c_dbl_p, _c_dbl_p]
         L.or_create.argtypes = [ctypes.c_int] * 7
@@ -175,6 +179,23 @@ def force_field(shape, periodic, V=None, gbody=(0.0, 0.0, 0.0)):
     return F
 
 
+def visc_force(shape, periodic, sigma, n, u, gpair, solid=None):
+    """C^{a,visc} [M, 3, N] from n [M, N], velocities u [M, 3, N] and g_ab [M, M, N]."""
+    nx, ny, nz = shape
+    N = nx * ny * nz
+    n = _dbl(n).reshape(-1, N)
+    M = n.shape[0]
+    uu = _dbl(u).reshape(M, 3, N)
+    gp = _dbl(gpair).reshape(M, M, N)
+    sig = _dbl(sigma)
+    out = np.zeros((M, 3, N))
+    s = _solid(solid, N)
+    lib().or_visc_force(nx, ny, nz, _p(_per(periodic), ctypes.c_int), _p(s, ctypes.c_uint8), M,
+                        _p(sig, ctypes.c_double), _p(n, ctypes.c_double), _p(uu, ctypes.c_double),
+                        _p(gp, ctypes.c_double), _p(out, ctypes.c_double))
+    return out
+
+
 def quasipressure(shape, periodic, sigma, n, V, gbody, solid=None):
     """Pi^a = n^a - beta * trapezoidal path integral of C^{a,mf} + n^a F^a (x, then y, then z from the
     origin); n and V [M, N] (V the full potential of each species), gbody [M, 3].  Returns [M, N]."""
@@ -239,6 +260,10 @@ class Sim:
 
     def set_consistent_moments(self, on):
         lib().or_set_consistent_moments(self._h, int(bool(on)))
+
+    def set_visc(self, on):
+        if lib().or_set_visc(self._h, int(bool(on))) != 0:
+            raise ValueError("C^visc needs the DD-TR scheme")
 
     def set_scheme(self, scheme):
         """0 DD-TR (default), 1 SD-TR, 2 SD-EU, 3 DD-EU (Sec. "Results": single or double distribution,

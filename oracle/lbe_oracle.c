@@ -313,6 +313,53 @@ void or_shell_force(int nx, int ny, int nz, const int *per, const uint8_t *solid
     free(K);
 }
 
+/* Viscous part of the Enskog force (Appendix, C^{alpha,visc}): for hard spheres
+ *   C^{a,visc}(r) = n_a(r) sum_b 2 sigma_ab^2 sqrt(m k_B T / pi)
+ *                   integral dk^ k^ g_ab n_b(r + sigma k^) k^.(u_b(r + sigma k^) - u_b(r)),
+ * on the lattice with the shell K_sigma, unit vectors e/|e|, the shell weight
+ * w_sigma and the endpoint-averaged contact value of the mean-field force.
+ * Neighbours outside a non-periodic axis or on solid nodes carry n_b = 0.
+ * u [M][3][N]; V [M][3][N]. */
+void or_visc_force(int nx, int ny, int nz, const int *per, const uint8_t *solid, int M,
+                   const double *sigma, const double *n, const double *u, const double *gpair, double *V) {
+    grid_t g = {{nx, ny, nz}, {per[0], per[1], per[2]}};
+    long N = nsites(&g);
+    int cap = 16384;
+    int *K = (int *)malloc(sizeof(int) * 3 * cap);
+    for (long t = 0; t < (long)M * 3 * N; ++t) V[t] = 0.0;
+    for (int a = 0; a < M; ++a) {
+        for (int b = 0; b < M; ++b) {
+            double sab = 0.5 * (sigma[a] + sigma[b]);
+            if (!(sab > 0.0)) continue;
+            int k = or_shell(sab, K, cap);
+            double wab = or_shell_weight(sab);
+            double pre = 2.0 * sab * sab * sqrt(KT / PI) * wab;
+            const double *gab = gpair + ((long)a * M + b) * N;
+            const double *nb = n + (long)b * N;
+            const double *ub = u + (long)b * 3 * N;
+            for (long i = 0; i < N; ++i) {
+                int x, y, z;
+                coords(&g, i, &x, &y, &z);
+                double sum[3] = {0.0, 0.0, 0.0};
+                for (int t = 0; t < k; ++t) {
+                    int ex = K[3 * t], ey = K[3 * t + 1], ez = K[3 * t + 2];
+                    long s = site(&g, x + ex, y + ey, z + ez);
+                    if (s < 0 || (solid && solid[s])) continue;
+                    double len = sqrt((double)(ex * ex + ey * ey + ez * ez));
+                    double e[3] = {ex / len, ey / len, ez / len};
+                    double gbar = 0.5 * (gab[i] + gab[s]);
+                    double edu = 0.0;
+                    for (int c = 0; c < 3; ++c) edu += e[c] * (ub[(long)c * N + s] - ub[(long)c * N + i]);
+                    for (int c = 0; c < 3; ++c) sum[c] += e[c] * gbar * nb[s] * edu;
+                }
+                double na = (solid && solid[i]) ? 0.0 : n[(long)a * N + i];
+                for (int c = 0; c < 3; ++c) V[((long)a * 3 + c) * N + i] += na * pre * sum[c];
+            }
+        }
+    }
+    free(K);
+}
+
 /* External force from a potential (Sec. "Ideal fluid": F = -grad U) plus a
  * uniform body force g.  The gradient is the isotropic D3Q19 stencil
  * grad_h V(r) = (1/c_s^2) sum_p w_p c_p V(r + c_p); a neighbour outside a
@@ -392,6 +439,7 @@ typedef struct {
     double sigma[MAXS], tau[MAXS];
     double gbody[MAXS][3];
     int consistent_moments;
+    int visc;            /* 1: add C^{visc} of the tilde velocities to the force terms */
     int scheme;          /* 0 DD-TR, 1 SD-TR, 2 SD-EU, 3 DD-EU */
     uint8_t *solid;      /* [N] */
     double *V;           /* [M][N] external potential per species */
@@ -400,6 +448,7 @@ typedef struct {
     double *fpost, *gpost;
     /* per-step work fields */
     double *n, *gpair, *Cmf, *F, *J, *Pi;
+    double *Cvisc, *ut;  /* C^{visc} [M][3][N] and the tilde velocities J~/n [M][3][N] */
     int flux_axis, flux_plane;
     double flux_sum[MAXS];
     long flux_count;
@@ -429,6 +478,8 @@ or_sim *or_create(int nx, int ny, int nz, int px, int py, int pz, int M) {
     s->F = (double *)calloc((size_t)M * 3 * N, sizeof(double));
     s->J = (double *)calloc((size_t)M * 3 * N, sizeof(double));
     s->Pi = (double *)calloc((size_t)M * N, sizeof(double));
+    s->Cvisc = (double *)calloc((size_t)M * 3 * N, sizeof(double));
+    s->ut = (double *)calloc((size_t)M * 3 * N, sizeof(double));
     s->flux_axis = 0;
     s->flux_plane = -1;
     return s;
@@ -439,6 +490,7 @@ void or_destroy(or_sim *s) {
     free(s->solid); free(s->V); free(s->phi); free(s->amp);
     free(s->f); free(s->gd); free(s->fpost); free(s->gpost);
     free(s->n); free(s->gpair); free(s->Cmf); free(s->F); free(s->J); free(s->Pi);
+    free(s->Cvisc); free(s->ut);
     free(s);
 }
 
@@ -479,8 +531,16 @@ int or_set_consistent_moments(or_sim *s, int on) {
 
 enum { DD_TR = 0, SD_TR = 1, SD_EU = 2, DD_EU = 3 };
 
+/* C^{visc} on (DD-TR only): it enters the moment recovery and both sources
+ * beside n F (Sec. "Hard sphere fluid mixture": J, S_f, S_g). */
+int or_set_visc(or_sim *s, int on) {
+    if (on && s->scheme != 0) return -1;
+    s->visc = on ? 1 : 0;
+    return 0;
+}
+
 int or_set_scheme(or_sim *s, int scheme) {
-    if (scheme < DD_TR || scheme > DD_EU) return -1;
+    if (scheme < DD_TR || scheme > DD_EU || (s->visc && scheme != DD_TR)) return -1;
     s->scheme = scheme;
     return 0;
 }
@@ -553,6 +613,20 @@ static void compute_moments(or_sim *s) {
         }
     or_contact_values(s->g.n[0], s->g.n[1], s->g.n[2], s->g.per, s->solid, M, s->sigma, s->n, s->gpair);
     or_shell_force(s->g.n[0], s->g.n[1], s->g.n[2], s->g.per, s->solid, M, s->sigma, s->n, s->gpair, s->Cmf);
+    if (s->visc) {
+        /* C^{visc} of the tilde moments (the collision functional taken at M~): u~ = J~/n */
+        for (int a = 0; a < M; ++a)
+            for (long i = 0; i < N; ++i) {
+                double Jt[3] = {0.0, 0.0, 0.0};
+                double nn = s->n[(long)a * N + i];
+                if (!s->solid[i])
+                    for (int p = 0; p < Q; ++p)
+                        for (int c = 0; c < 3; ++c) Jt[c] += CV[p][c] * s->gd[((long)a * Q + p) * N + i];
+                for (int c = 0; c < 3; ++c) s->ut[((long)a * 3 + c) * N + i] = nn > 0.0 ? Jt[c] / nn : 0.0;
+            }
+        or_visc_force(s->g.n[0], s->g.n[1], s->g.n[2], s->g.per, s->solid, M, s->sigma, s->n, s->ut, s->gpair,
+                      s->Cvisc);
+    }
     for (int a = 0; a < M; ++a)
         for (long i = 0; i < N; ++i) {
             double Pit = 0.0, Jt[3] = {0.0, 0.0, 0.0};
@@ -567,7 +641,8 @@ static void compute_moments(or_sim *s) {
             double Cm[3], nF[3];
             for (int c = 0; c < 3; ++c) {
                 Cm[c] = s->Cmf[((long)a * 3 + c) * N + i];
-                nF[c] = nn * s->F[((long)a * 3 + c) * N + i];
+                /* n F, plus C^{visc} where it is on: the two enter every formula together */
+                nF[c] = nn * s->F[((long)a * 3 + c) * N + i] + (s->visc ? s->Cvisc[((long)a * 3 + c) * N + i] : 0.0);
             }
             double J[3];
             for (int c = 0; c < 3; ++c) {
@@ -649,7 +724,7 @@ static void one_step(or_sim *s) {
             for (int c = 0; c < 3; ++c) {
                 ua[c] = (nn > 0.0) ? s->J[((long)a * 3 + c) * N + i] / nn : 0.0;
                 Cm[c] = s->Cmf[((long)a * 3 + c) * N + i];
-                nF[c] = nn * s->F[((long)a * 3 + c) * N + i];
+                nF[c] = nn * s->F[((long)a * 3 + c) * N + i] + (s->visc ? s->Cvisc[((long)a * 3 + c) * N + i] : 0.0);
             }
             double omega = 1.0 / (s->tau[a] - 0.5); /* omega h, h = 1 (TR) */
             double omega_eu = 1.0 / s->tau[a];       /* omega h of the Euler update */

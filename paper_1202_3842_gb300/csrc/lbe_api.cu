@@ -92,6 +92,9 @@ struct lbe_ctx {
     int specNS = 0;  // shells with a spectrum; the ball spectra follow them in specTab
     SpecPairs specPairs{};
     Buf specR, specZ, specW, specTab, specWork;
+    // viscous Enskog force (enable_visc): shell tables of the pairs, tilde velocities, effective force
+    ViscPairs vp{};
+    Buf veoff, vehat, vut, Feff;
     // the discrete adjoint's spectral shell transpose, kept between calls until the pairs change
     SpectralShell *aspec = nullptr;
     int aL[3] = {0, 0, 0};
@@ -511,6 +514,48 @@ lbe_status spectral_force(lbe_ctx *c, void *Pbase, void *xibase) {
     return LBE_OK;
 }
 
+// Shell tables of the viscous force (the pairs' shells, offsets and unit vectors in FP64) and its
+// fields: the tilde velocities and the effective force F + C^visc / n.
+lbe_status visc_setup(lbe_ctx *c) {
+    const size_t rb = real_bytes(c);
+    const long long N = c->g.N;
+    ViscPairs vp{};
+    vp.M = c->M;
+    vp.npairs = (int)c->pairs.size();
+    std::vector<int> eo;
+    std::vector<double> eh;
+    for (int q = 0; q < vp.npairs; ++q) {
+        const PairShell &ps = c->pairs[q];
+        vp.a[q] = ps.a;
+        vp.b[q] = ps.b;
+        vp.first[q] = (int)(eo.size() / 3);
+        const int S = ps.S;
+        for (int z = -S; z <= S; ++z)
+            for (int y = -S; y <= S; ++y)
+                for (int x = -S; x <= S; ++x)
+                    if (in_shell(S, x, y, z)) {
+                        const double len = std::sqrt((double)(x * x + y * y + z * z));
+                        eo.insert(eo.end(), {x, y, z});
+                        eh.insert(eh.end(), {x / len, y / len, z / len});
+                    }
+        vp.count[q] = (int)(eo.size() / 3) - vp.first[q];
+        vp.pre[q] = 2.0 * (double)S * (double)S * std::sqrt(kKT / kPi) * shell_weight(S);
+    }
+    c->vp = vp;
+    TRY(dev_alloc(c, c->veoff, sizeof(int) * std::max<size_t>(eo.size(), 3)));
+    TRY(dev_alloc(c, c->vehat, sizeof(double) * std::max<size_t>(eh.size(), 3)));
+    TRY(dev_alloc(c, c->vut, rb * 3 * (size_t)c->M * N));
+    TRY(dev_alloc(c, c->Feff, rb * 3 * (size_t)c->M * N));
+    if (!eo.empty()) {
+        CK(cudaMemcpyAsync(c->veoff.p, eo.data(), sizeof(int) * eo.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy viscous shell offsets");
+        CK(cudaMemcpyAsync(c->vehat.p, eh.data(), sizeof(double) * eh.size(), cudaMemcpyHostToDevice, c->stream),
+           "copy viscous shell vectors");
+        CK(cudaStreamSynchronize(c->stream), "stream sync");  // the host tables die here
+    }
+    return LBE_OK;
+}
+
 // Set up everything that depends on the species, geometry and potentials:
 // halo width, padded fields, tensor maps, ball tables, force field.
 lbe_status prepare(lbe_ctx *c) {
@@ -630,6 +675,7 @@ lbe_status prepare(lbe_ctx *c) {
         spectral_destroy(c->aspec);  // the adjoint's transpose plans and tables follow the pairs
         c->aspec = nullptr;
         if (c->spectral) TRY(spectral_setup(c));
+        if (c->cfg.enable_visc) TRY(visc_setup(c));
         c->fields_dirty = false;
     }
     if (c->force_dirty) {
@@ -667,7 +713,7 @@ StepParams step_params(const lbe_ctx *c) {
 // npad, gab, gnpad, C.  With Pbase, the shell kernels also store P of every
 // pair into Pbase [npairs][3][N], and with xibase the contact kernel stores
 // xi2, xi3 into xibase [2][N] (both for the adjoint).
-lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = nullptr, void *xibase = nullptr) {
+lbe_status force_stage_core(lbe_ctx *c, const void *pop, void *Pbase, void *xibase) {
     const bool f64 = prec_fp64(c->prec);
     const size_t rb = real_bytes(c);
     if (!pop) pop = c->pop[c->cur].p;
@@ -717,6 +763,23 @@ lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = null
     return LBE_OK;
 }
 
+// The force field the collide and the getters use: F, or F + C^visc / n with the viscous force on.
+const void *force_field(const lbe_ctx *c) { return c->cfg.enable_visc && !c->pairs.empty() ? c->Feff.p : c->F.p; }
+
+lbe_status force_stage(lbe_ctx *c, const void *pop = nullptr, void *Pbase = nullptr, void *xibase = nullptr) {
+    if (!pop) pop = c->pop[c->cur].p;
+    TRY(force_stage_core(c, pop, Pbase, xibase));
+    if (c->cfg.enable_visc && !c->pairs.empty()) {
+        StageTimer t(c, LBE_STAGE_SHELL);
+        LAUNCH(launch_visc(c->prec, c->g, pop, (const uint32_t *)c->mask.p, c->npad.p, c->gab.p, c->F.p,
+                           step_params(c), c->vp, (const int *)c->veoff.p, (const double *)c->vehat.p, c->vut.p,
+                           c->Feff.p, c->stream),
+               "viscous force");
+        c->launches += 1;  // two kernels
+    }
+    return LBE_OK;
+}
+
 int plane_size(const lbe_ctx *c) {
     const Grid &g = c->g;
     return c->flux_axis == 0 ? g.ny * g.nz : (c->flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
@@ -748,7 +811,7 @@ lbe_status state_moments(lbe_ctx *c, double **n, double **J) {
     *J = *n + (long long)c->M * N;
     StepParams sp = step_params(c);
     if (sp.scheme == LBE_DD_TR) {
-        LAUNCH(launch_moments(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, c->F.p, sp, *n,
+        LAUNCH(launch_moments(c->prec, c->g, c->pop[c->cur].p, (const uint32_t *)c->mask.p, c->C.p, force_field(c), sp, *n,
                               *J, c->stream),
                "moments kernel");
     } else {
@@ -766,7 +829,7 @@ lbe_status step_once(lbe_ctx *c, const StepParams &sp, int psize) {
         StageTimer tm(c, LBE_STAGE_COLLIDE);
         if (sp.scheme == LBE_DD_TR) {
             LAUNCH(launch_collide(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p, (const uint32_t *)c->mask.p,
-                                  c->solid_links, c->C.p, c->F.p, sp, (double *)c->flux_buf.p, c->stream),
+                                  c->solid_links, c->C.p, force_field(c), sp, (double *)c->flux_buf.p, c->stream),
                    "collide kernel");
         } else {
             LAUNCH(launch_collide_ablation(c->prec, c->g, c->pop[c->cur].p, c->pop[1 - c->cur].p,
@@ -832,7 +895,8 @@ lbe_status lbe_create(const lbe_config *cfg, const lbe_allocator *allocator, voi
         if (cfg->consistent_moments)
             return fail(nullptr, LBE_ERR_INVALID_ARG, "consistent_moments applies to the DD-TR scheme only");
     }
-    if (cfg->enable_visc) return fail(nullptr, LBE_ERR_UNSUPPORTED, "the viscous Enskog force is not implemented");
+    if (cfg->enable_visc && cfg->scheme != LBE_DD_TR)
+        return fail(nullptr, LBE_ERR_UNSUPPORTED, "the viscous Enskog force belongs to the DD-TR scheme");
     if (allocator && (!allocator->alloc || !allocator->free))
         return fail(nullptr, LBE_ERR_INVALID_ARG, "allocator needs both alloc and free");
 
@@ -911,7 +975,7 @@ void lbe_destroy(lbe_ctx *c) {
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
                   &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec,
                   &c->specR, &c->specZ, &c->specW, &c->specTab, &c->specWork,
-                  &c->aR, &c->aZ, &c->aW, &c->aTab, &c->aWork};
+                  &c->aR, &c->aZ, &c->aW, &c->aTab, &c->aWork, &c->veoff, &c->vehat, &c->vut, &c->Feff};
     spectral_destroy(c->spec);
     c->spec = nullptr;
     spectral_destroy(c->aspec);
@@ -1468,6 +1532,8 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
     if (!(c->prec == Prec::F32 || c->prec == Prec::F64))
         return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint runs on FP64 or FP32 populations only");
     if (c->cfg.scheme != LBE_DD_TR) return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint is that of the DD-TR scheme");
+    if (c->cfg.enable_visc)
+        return fail(c, LBE_ERR_UNSUPPORTED, "the adjoint does not transpose the viscous Enskog force");
     TRY(prepare(c));
     const bool f64 = prec_fp64(c->prec);
     // K3 transposed: the stencil tiles, or the spectral form (the same sums as correlations with the

@@ -205,6 +205,19 @@ cudaError_t launch_adj_contact_prep(bool fp64, const Grid &g, const ContactParam
 cudaError_t launch_adj_amp(bool fp64, const Grid &g, int M, const void *lF, const double *phi, double *out,
                            cudaStream_t st);
 
+// Viscous Enskog force folded into an effective force field (lbe_visc.cu): shell points of every
+// ordered pair in eoff [3 per point] / ehat [3 per point], pair q's run first[q] .. first[q] + count[q].
+struct ViscPairs {
+    int M, npairs;
+    int a[MAXS * MAXS], b[MAXS * MAXS];
+    int first[MAXS * MAXS], count[MAXS * MAXS];
+    double pre[MAXS * MAXS];  // 2 sigma_ab^2 sqrt(k_B T / pi) w_ab (times n_a / n_a: C^visc / n_a)
+};
+// u~ [M][3][N] scratch; Feff [M][3][N] = F + C^visc / n
+cudaError_t launch_visc(Prec p, const Grid &g, const void *pop, const uint32_t *mask, const void *npad,
+                        const void *gab, const void *F, const StepParams &sp, const ViscPairs &vp, const int *eoff,
+                        const double *ehat, void *ut, void *Feff, cudaStream_t st);
+
 // K3 by fast Fourier transforms (lbe_spectral.cu).
 struct SpecPairs {
     int M, npairs;

@@ -174,7 +174,7 @@ SCHEMES = {"dd_tr": LBE_DD_TR, "sd_tr": LBE_SD_TR, "sd_eu": LBE_SD_EU, "dd_eu": 
 
 
 def lbe_create(shape, periodic=(1, 1, 1), nspecies=1, precision="fp32", consistent_moments=0, check_every=0,
-               allocator=None, stream=None, scheme="dd_tr"):
+               allocator=None, stream=None, scheme="dd_tr", visc=False):
     cfg = lbe_config()
     cfg.nx, cfg.ny, cfg.nz = [int(v) for v in shape]
     for k in range(3):
@@ -182,7 +182,7 @@ def lbe_create(shape, periodic=(1, 1, 1), nspecies=1, precision="fp32", consiste
     cfg.nspecies = int(nspecies)
     cfg.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     cfg.scheme = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
-    cfg.enable_visc = 0
+    cfg.enable_visc = int(bool(visc))
     cfg.consistent_moments = int(bool(consistent_moments))
     cfg.check_every = int(check_every)
     out = ctypes.c_void_p()
@@ -419,7 +419,7 @@ class Simulation:
     """One lattice on the current CUDA device; every method is one C ABI call."""
 
     def __init__(self, shape, periodic=(1, 1, 1), nspecies=1, precision="fp32", consistent_moments=False,
-                 check_every=0, use_torch_allocator=True, stream=None, scheme="dd_tr"):
+                 check_every=0, use_torch_allocator=True, stream=None, scheme="dd_tr", visc=False):
         self.shape = tuple(int(v) for v in shape)
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
         self.M = int(nspecies)
@@ -430,7 +430,7 @@ class Simulation:
         if stream is None and use_torch_allocator:
             stream = current_stream_handle()
         self._h = lbe_create(self.shape, periodic, nspecies, precision, consistent_moments, check_every,
-                             self._alloc, stream, scheme)
+                             self._alloc, stream, scheme, visc)
 
     def close(self):
         if getattr(self, "_h", None):

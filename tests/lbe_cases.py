@@ -20,11 +20,11 @@ def case_channel(shape, sigmas, eta, taus, width, length, body=1e-6, wall_amp_kT
 SCHEME_IDS = {"dd_tr": 0, "sd_tr": 1, "sd_eu": 2, "dd_eu": 3}
 
 
-def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_tr", shell="auto"):
+def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_tr", shell="auto", visc=False):
     from paper_1202_3842_gb300 import lbe
     M = len(w["sigma"])
     sim = lbe.Simulation(w["shape"], w["periodic"], M, precision, consistent_moments=consistent,
-                         check_every=check_every, scheme=scheme)
+                         check_every=check_every, scheme=scheme, visc=visc)
     if shell != "auto":
         sim.set_shell_method(shell)
     sim.set_geometry(arrays["solid"])
@@ -38,12 +38,13 @@ def setup_gpu(w, arrays, precision, consistent=False, check_every=0, scheme="dd_
     return sim
 
 
-def setup_oracle(w, arrays, consistent=False, scheme="dd_tr"):
+def setup_oracle(w, arrays, consistent=False, scheme="dd_tr", visc=False):
     M = len(w["sigma"])
     sim = oracle.Sim(w["shape"], w["periodic"], M)
     sim.set_geometry(arrays["solid"])
     sim.set_consistent_moments(consistent)
     sim.set_scheme(SCHEME_IDS[scheme])
+    sim.set_visc(visc)
     for a in range(M):
         sim.set_species(a, w["sigma"][a], w["tau"][a])
         sim.set_potential(a, arrays["V"][a])

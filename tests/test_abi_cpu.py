@@ -63,6 +63,7 @@ def test_bad_config_is_rejected_before_device_use(L):
     assert L.lbe_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == 1
     cfg.nspecies = 1
     cfg.enable_visc = 1
+    cfg.scheme = lbe.LBE_SD_EU  # the viscous force belongs to the DD-TR scheme
     assert L.lbe_create(ctypes.byref(cfg), None, None, ctypes.byref(out)) == 2
 
 
