@@ -74,6 +74,7 @@ def parse():
     p.add_argument("--adjoint-only", action="store_true", help="time only the adjoint against the forward")
     p.add_argument("--adjoint-steps", type=int, default=2000)
     p.add_argument("--adjoint-ckpt", type=int, default=100)
+    p.add_argument("--visc", action="store_true", help="add the viscous Enskog force (an option of the scheme)")
     p.add_argument("--shell", default="auto", choices=["auto", "direct", "spectral"],
                    help="K3 method: stencil sum, FFT convolution, or the library's choice")
     return p.parse_args()
@@ -307,10 +308,10 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------
-def make_sim(w, arrays, prec, shell="auto"):
+def make_sim(w, arrays, prec, shell="auto", visc=False):
     from paper_1202_3842_gb300 import lbe
     M = len(w["sigma"])
-    sim = lbe.Simulation(w["shape"], w["periodic"], M, prec)
+    sim = lbe.Simulation(w["shape"], w["periodic"], M, prec, visc=visc)
     if shell != "auto":
         sim.set_shell_method(shell)
     if arrays["solid"].any():
@@ -373,7 +374,7 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     M = len(w["sigma"])
     nx, ny, nz = w["shape"]
     N = nx * ny * nz
-    sim = make_sim(w, arrays, prec, getattr(args, "shell", "auto"))
+    sim = make_sim(w, arrays, prec, getattr(args, "shell", "auto"), getattr(args, "visc", False))
     shell_method = sim.shell_method()
     sim.step(warmup)
     torch.cuda.synchronize()
@@ -475,7 +476,7 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     res = {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
            "mlups_nodes": value / M,
            "config": {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "nodes": N,
-                      "species": M, "shell_method": shell_method,
+                      "species": M, "shell_method": shell_method, "viscous_force": bool(getattr(args, "visc", False)),
                       "l2": "inputs larger than L2: population buffers %.2f GB each" % (N * M * 2 * QPOP * sb / 1e9),
                       "parallelism": "replicas only (one independent lattice per GPU)" if world > 1 else "1 GPU"},
            "roofline": roof,
