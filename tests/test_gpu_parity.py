@@ -229,9 +229,10 @@ def test_fp32_channel_flux_against_oracle():
 
 
 @pytest.mark.parametrize("prec,tol", [("bf16", 1e-2), ("fp16", 1e-3)])
-def test_shifted_16bit_against_oracle(prec, tol):
+@pytest.mark.parametrize("shell", ["direct", "spectral"])
+def test_shifted_16bit_against_oracle(prec, tol, shell):
     w, arr = case_channel((64, 24, 20), (4.0, 6.0), 0.25, (1.0, 1.0), 10, 16, body=1e-5)
-    g = setup_gpu(w, arr, prec)
+    g = setup_gpu(w, arr, prec, shell=shell)
     o = setup_oracle(w, arr)
     g.set_flux_plane(0, 32)
     o.set_flux_plane(0, 32)

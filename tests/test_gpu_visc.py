@@ -84,3 +84,17 @@ def test_viscous_force_is_rejected_where_it_does_not_apply():
     with pytest.raises(lbe.LbeError) as e:
         g.adjoint_flux_gradient(2, 1, 0, 6)
     assert e.value.status == lbe.LBE_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 1e-2), ("fp16", 1e-3)])
+def test_shifted_16bit_storage_with_viscous_force(prec, tol):
+    """16-bit shifted populations with FP32 arithmetic, the viscous force on: the densities against the
+    FP64 oracle within the bounds of the 16-bit storage test (bf16 1e-2, fp16 1e-3 after 30 steps)."""
+    w, arr = case_channel((40, 22, 18), (4.0, 6.0), 0.25, (1.0, 0.8), 10, 12, body=1e-5)
+    g = setup_gpu(w, arr, prec, visc=True)
+    o = setup_oracle(w, arr, visc=True)
+    g.step(30)
+    o.step(30)
+    obs = o.observe()
+    for a in range(2):
+        assert rel_err(g.density(a), obs["n"][a]) <= tol
