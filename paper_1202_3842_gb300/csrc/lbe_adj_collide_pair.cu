@@ -43,7 +43,7 @@ __device__ __forceinline__ T partner(T v) {
 }
 
 template <typename S, typename T, int M>
-__global__ void __launch_bounds__(ACP, sizeof(T) == 4 ? 2 : 1)
+__global__ void __launch_bounds__(ACP, sizeof(T) == 4 ? 3 : 1)
     k_adj_collide_pair(Grid g, const S *__restrict__ post, const uint32_t *__restrict__ mask,
                        const T *__restrict__ C, const T *__restrict__ F, AdjParams ap, const T *__restrict__ lYf_in,
                        const T *__restrict__ lYg_in, const T *__restrict__ lnd_in, T *__restrict__ lYf_out,
@@ -106,7 +106,12 @@ __global__ void __launch_bounds__(ACP, sizeof(T) == 4 ? 2 : 1)
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
 
     // ---- pass B: collision transposed
-    T lfk[Q], lgk[Q];
+    // FP32: the gathered adjoint populations wait for the last pass in shared memory (39 KB per CTA),
+    // which leaves the registers for three CTAs per SM; FP64 keeps them in registers
+    constexpr bool SMEM = sizeof(T) == 4;
+    __shared__ T sl[SMEM ? 2 : 1][SMEM ? Q : 1][SMEM ? ACP : 1];
+    T lfk[SMEM ? 1 : Q], lgk[SMEM ? 1 : Q];
+    const int tid = threadIdx.x;
     T lu[3] = {0, 0, 0}, lua[3] = {0, 0, 0}, lCs[3] = {0, 0, 0}, lnFs[3] = {0, 0, 0}, lns = 0, lPis = 0;
     if (fluid) {
         const T uau = ua[0] * u[0] + ua[1] * u[1] + ua[2] * u[2];
@@ -124,8 +129,13 @@ __global__ void __launch_bounds__(ACP, sizeof(T) == 4 ? 2 : 1)
                     constexpr T w = (T)wq(P);
                     const T lfs = gather_post_pair<T, P>(lYf, lnd, g.N, i, o, m);
                     const T lgs = gather_post_pair<T, P>(lYg, nullptr, g.N, i, o, m);
-                    lfk[P] = lfs;
-                    lgk[P] = lgs;
+                    if constexpr (SMEM) {
+                        sl[0][P][tid] = lfs;
+                        sl[1][P][tid] = lgs;
+                    } else {
+                        lfk[P] = lfs;
+                        lgk[P] = lgs;
+                    }
                     const T cua = cdot<T, P>(ua);
                     const T cu = cdot<T, P>(u);
                     const T cX = cdot<T, P>(X);
@@ -235,8 +245,10 @@ __global__ void __launch_bounds__(ACP, sizeof(T) == 4 ? 2 : 1)
     [&]<int... P>(std::integer_sequence<int, P...>) {
         (
             [&] {
-                of[(long long)P * g.N] = om1 * lfk[P] + ln;
-                og[(long long)P * g.N] = om1 * lgk[P] + lPit + cdot<T, P>(lJ);
+                const T lfs = SMEM ? sl[0][P][tid] : lfk[SMEM ? 0 : P];
+                const T lgs = SMEM ? sl[1][P][tid] : lgk[SMEM ? 0 : P];
+                of[(long long)P * g.N] = om1 * lfs + ln;
+                og[(long long)P * g.N] = om1 * lgs + lPit + cdot<T, P>(lJ);
             }(),
             ...);
     }(std::make_integer_sequence<int, Q>{});

@@ -24,13 +24,15 @@ __device__ __forceinline__ void node_xyz(const Grid &g, long long i, int &x, int
 }
 
 // Linear offsets to the six neighbours with periodic wrap (a closed axis wraps
-// too; such links are masked, so the wrapped address is never used).
+// too; such links are masked, so the wrapped address is never used).  Lattices
+// hold fewer than 2^31 nodes, so an offset, and the sum of three that reaches
+// another node, fits in 32 bits (six registers fewer than 64-bit offsets).
 struct NbrOff {
-    long long xm, xp, ym, yp, zm, zp;
+    int xm, xp, ym, yp, zm, zp;
 };
 __device__ __forceinline__ NbrOff nbr_offsets(const Grid &g, int x, int y, int z) {
     NbrOff o;
-    const long long sx = 1, sy = g.nx, sz = (long long)g.nx * g.ny;
+    const int sx = 1, sy = g.nx, sz = g.nx * g.ny;
     o.xm = (x > 0) ? -sx : (g.nx - 1) * sx;
     o.xp = (x < g.nx - 1) ? sx : -(g.nx - 1) * sx;
     o.ym = (y > 0) ? -sy : (g.ny - 1) * sy;
@@ -42,7 +44,7 @@ __device__ __forceinline__ NbrOff nbr_offsets(const Grid &g, int x, int y, int z
 // Offset of the source node r - c_p.
 template <int P>
 __device__ __forceinline__ long long src_off(const NbrOff &o) {
-    long long d = 0;
+    int d = 0;
     if constexpr (cx(P) == 1) d += o.xm;
     if constexpr (cx(P) == -1) d += o.xp;
     if constexpr (cy(P) == 1) d += o.ym;
