@@ -24,8 +24,10 @@ namespace lbe {
 
 constexpr int NTP = 256;  // threads per CTA: 128 nodes (two species) or 256 (one)
 
+// FP32 arithmetic: four CTAs of 256 threads per SM for one species (0.95 -> 0.88 ms on the 256^3
+// well, with some spills at 64 registers), three for two (four made the two-species launch slower).
 template <typename S, typename T, int M, bool SOLID>
-__global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     k_collide_pair(Grid g, const S *__restrict__ src, S *__restrict__ dst, const uint32_t *__restrict__ mask,
                    const T *__restrict__ C, const T *__restrict__ F, StepParams sp, double *__restrict__ flux_buf) {
     static_assert(M == 1 || M == 2, "one or two species");
