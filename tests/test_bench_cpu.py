@@ -1,6 +1,7 @@
 """Host logic of bench.py (no GPU): the spectral grid sizes, the traffic entries' source check, and the
 per-stage roofline figures."""
 import json
+
 import bench
 
 
