@@ -15,6 +15,7 @@ numbers; ``python -m paper_1202_3842_gb300.studies <study> [--quick]`` prints on
 - ``divergence``: max and mean |div u| in the bottleneck channel after a long run, per scheme.
 - ``init``: the transient of the spurious current from the rest state and from the quasi-pressure
   state of the second distribution.
+- ``visc``: stability with and without the viscous Enskog force.
 
 Scheme names: ``dd_tr`` (the method, printed moment recovery), ``dd_tr_c`` (DD-TR with the
 map-consistent recovery), ``sd_tr``, ``sd_eu``, ``dd_eu``.
@@ -232,6 +233,47 @@ def init(xis=(6, 12), sigma=4.0, eta=0.2, steps=2000, prec="fp64", schemes=("dd_
     return out
 
 
+def visc(cases=("well48", "channel128", "well24"), steps=600, prec="fp32", check=20):
+    """Stability with and without the viscous Enskog force (an option of the DD-TR scheme): for each case
+    the step at which a negative density appears (checked every `check` steps), or max|u|/v_T after
+    `steps` steps.  Cases: "well48" (48^3, sigma 6, packing 0.3, Gaussian well 2 k_BT of radius 12,
+    tau 0.8), "channel128" and "well24" (the named workloads of inputs.py), "well256"."""
+    builders = {
+        "well48": lambda: inputs.well_workload((48, 48, 48), 6.0, 0.3, 0.8, 2.0, 12.0),
+        "channel128": inputs.WORKLOADS["channel128"],
+        "well24": inputs.WORKLOADS["well24"],
+        "well256": inputs.WORKLOADS["well256"],
+    }
+    out = {}
+    for name in cases:
+        w = builders[name]()
+        arr = inputs.build_workload(w)
+        M = len(w["sigma"])
+        out[name] = {}
+        for on in (False, True):
+            sim = lbe.Simulation(w["shape"], w["periodic"], M, prec, visc=on, check_every=check)
+            sim.set_geometry(arr["solid"])
+            for a in range(M):
+                sim.set_species(a, w["sigma"][a], w["tau"][a])
+                sim.set_potential(a, arr["V"][a])
+                sim.set_body_force(a, w["body"][a])
+            sim.set_wall_potential(arr["phi"], arr["amp"])
+            for a in range(M):
+                sim.init_density(a, arr["n"][a])
+            done = 0
+            try:
+                while done < steps:
+                    sim.step(check)
+                    done += check
+                u = sim.velocity(-1)
+                res = {"stable_steps": done, "u": float(np.sqrt((u ** 2).sum(0)).max() / CS)}
+            except lbe.LbeError as e:
+                res = {"diverged_by_step": done + check, "error": str(e)}
+            sim.close()
+            out[name]["visc" if on else "plain"] = res
+    return out
+
+
 # Reduced sizes for a quick look (a few seconds each on one GPU).
 QUICK = {
     "spurious": dict(xis=(6,), steps=1000),
@@ -240,9 +282,10 @@ QUICK = {
     "ideal_gas": dict(xis=(4, 6), steps_per_L2=3),
     "divergence": dict(shape=(64, 32, 32), length=32, steps=1000),
     "init": dict(xis=(6,), steps=500),
+    "visc": dict(cases=("well48", "well24"), steps=200),
 }
 STUDIES = dict(spurious=spurious, mixture=mixture, stability=stability, ideal_gas=ideal_gas,
-               divergence=divergence, init=init)
+               divergence=divergence, init=init, visc=visc)
 
 
 def main(argv=None):

@@ -38,3 +38,13 @@ def test_ideal_gas_tr_current_below_euler():
         tr, eu = r["sd_tr"][xi], r["sd_eu"][xi]
         assert tr["J"] * 10 < eu["J"], (xi, tr, eu)
         assert 0.5 < tr["n"] / eu["n"] < 2.0, (xi, tr, eu)
+
+
+def test_viscous_force_study_runs_and_the_dense_well_diverges_no_later_without_it():
+    from paper_1202_3842_gb300 import studies
+    r = studies.visc(cases=("well48", "well24"), steps=200)
+    assert set(r) == {"well48", "well24"}
+    assert "stable_steps" in r["well24"]["plain"] and "stable_steps" in r["well24"]["visc"]
+    plain, visc = r["well48"]["plain"], r["well48"]["visc"]
+    assert "diverged_by_step" in visc
+    assert visc["diverged_by_step"] <= plain.get("diverged_by_step", 10 ** 9)
