@@ -40,9 +40,15 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")  # JSON text
 FALLBACK_HBM_GBS = 6800.0
 FP64_NOMINAL_TFLOPS = 1.25
-SMS = 152
+SMS_NOMINAL = 152          # GB300; the run uses the device's own multiprocessor count
 FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
 QPOP = 19
+# Algorithmic flops of the fused collide (K4) per node and species, counted from its source
+# (csrc/lbe_collide_pair.cu): moments 63 (n, Pi~: 18 adds each; J~: 9 adds per component), recovery,
+# velocities and the isotropic terms 57, and per population 36 (t1 7, f_eq and g_eq 4, S_f 6, S_g 9,
+# the two TR updates 10) plus one add per dot product c_p . v on the 12 edge links (5 dot products).
+K4_FLOPS_PER_NODE_SPECIES = 63 + 57 + 19 * 36 + 12 * 5
 
 WORKLOAD_TEXT = {
     "well256": "D3Q19 256^3 periodic, 1 species, sigma 6, packing 0.3 (+-1% noise, seed 1202), Gaussian well "
@@ -72,6 +78,8 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-extra", action="store_true", help="skip the bounded spherical-well and adjoint lines")
     p.add_argument("--adjoint-only", action="store_true", help="time only the adjoint against the forward")
+    p.add_argument("--cpu-study", action="store_true",
+                   help="time only the OpenMP oracle on the 24^3 well, the 128x32x32 channel and the 256^3 well")
     p.add_argument("--adjoint-steps", type=int, default=2000)
     p.add_argument("--adjoint-ckpt", type=int, default=100)
     p.add_argument("--visc", action="store_true", help="add the viscous Enskog force (an option of the scheme)")
@@ -174,6 +182,13 @@ def shell_flops_per_node(S):
     return f + 3 * 4 + 2
 
 
+def ball_count(radius):
+    """Points of the averaging ball |d|^2 <= radius^2 of the contact values."""
+    R = int(math.floor(radius))
+    return sum(1 for z in range(-R, R + 1) for y in range(-R, R + 1) for x in range(-R, R + 1)
+               if x * x + y * y + z * z <= radius * radius)
+
+
 def source_hash(files):
     h = hashlib.sha256()
     for f in files:
@@ -209,10 +224,21 @@ def traffic_for(stage, workload, prec):
 # ---------------------------------------------------------------------------
 # CPU oracle leg
 # ---------------------------------------------------------------------------
-def oracle_sample_sim(w, arrays, L):
+def oracle_threads():
+    """Threads the OpenMP build of the oracle runs on: OMP_NUM_THREADS if set, else the usable host cores."""
+    try:
+        return int(os.environ["OMP_NUM_THREADS"])
+    except (KeyError, ValueError):
+        try:
+            return len(os.sched_getaffinity(0))
+        except AttributeError:
+            return os.cpu_count() or 1
+
+
+def oracle_sample_sim(w, arrays, L, openmp=False):
     """Oracle simulation of a bounded sample of workload w: for a spherical well, a periodic L^3 sub-box cut
     from its centre; for a channel, a channel of the same kind (walls, constriction of the same width,
-    same species and packing) of size (2L) x L x L."""
+    same species and packing) of size (2L) x L x L.  openmp: the OpenMP build of the same source."""
     import numpy as np
     import oracle
     from paper_1202_3842_gb300 import inputs
@@ -224,7 +250,7 @@ def oracle_sample_sim(w, arrays, L):
         ca["n"] = np.stack([inputs.uniform_density(cw["shape"], w["n0"][a], ca["solid"])
                             for a in range(len(w["sigma"]))])
         M = len(w["sigma"])
-        sim = oracle.Sim(cw["shape"], cw["periodic"], M)
+        sim = oracle.Sim(cw["shape"], cw["periodic"], M, openmp=openmp)
         sim.set_geometry(ca["solid"])
         for a in range(M):
             sim.set_species(a, w["sigma"][a], w["tau"][a])
@@ -243,7 +269,7 @@ def oracle_sample_sim(w, arrays, L):
         return f[np.ix_(zs, ys, xs)].reshape(-1)
 
     M = len(w["sigma"])
-    sim = oracle.Sim((L, L, L), (1, 1, 1), M)
+    sim = oracle.Sim((L, L, L), (1, 1, 1), M, openmp=openmp)
     for a in range(M):
         sim.set_species(a, w["sigma"][a], w["tau"][a])
         sim.set_potential(a, sub(arrays["V"][a]))
@@ -260,9 +286,7 @@ def sample_text(w, L):
     return "a %d^3 periodic sub-box cut from the centre of the %s workload" % (L, w.get("name", "?"))
 
 
-def cpu_baseline(w, arrays, L=32, min_s=10.0, max_steps=400):
-    sim, nodes = oracle_sample_sim(w, arrays, L)
-    M = len(w["sigma"])
+def _time_oracle(sim, min_s, max_steps):
     sim.step(1)
     t0 = time.perf_counter()
     n = 0
@@ -271,9 +295,54 @@ def cpu_baseline(w, arrays, L=32, min_s=10.0, max_steps=400):
         n += 1
         if time.perf_counter() - t0 >= min_s:
             break
-    dt = time.perf_counter() - t0
-    return {"value": nodes * M * n / dt / 1e6, "unit": "MLUPS/species", "cores": 1, "kind": "oracle",
-            "sample": "%d steps of %s, single-threaded FP64 C oracle" % (n, sample_text(w, L))}
+    return n, time.perf_counter() - t0
+
+
+def cpu_baseline(w, arrays, L=32, min_s=10.0, max_steps=400):
+    """The FP64 oracle as it stands on the host cores: the OpenMP build of its source on every usable core
+    (the reported value), and the single-threaded parity build for a few seconds beside it."""
+    M = len(w["sigma"])
+    sim, nodes = oracle_sample_sim(w, arrays, L, openmp=True)
+    n, dt = _time_oracle(sim, min_s, max_steps)
+    sim.close()
+    sim1, _ = oracle_sample_sim(w, arrays, L)
+    n1, dt1 = _time_oracle(sim1, 3.0, max_steps)
+    sim1.close()
+    return {"value": nodes * M * n / dt / 1e6, "unit": "MLUPS/species", "cores": oracle_threads(), "kind": "oracle",
+            "sample": "%d steps of %s, FP64 C oracle, OpenMP build on %d threads" % (n, sample_text(w, L),
+                                                                                     oracle_threads()),
+            "single_thread": {"value": nodes * M * n1 / dt1 / 1e6, "cores": 1, "steps": n1}}
+
+
+def cpu_study():
+    """The OpenMP oracle timed on the three workloads of the CPU-baseline plan: the 24^3 well (200 steps),
+    the 128x32x32 channel (20 steps) and the 256^3 well (5 steps, after one untimed step; the per-step time
+    extrapolates to a run)."""
+    import numpy as np
+    import oracle
+    from paper_1202_3842_gb300 import inputs
+    out = {"threads": oracle_threads()}
+    for name, steps in (("well24", 200), ("channel128", 20), ("well256", 5)):
+        w = inputs.WORKLOADS[name]()
+        a = inputs.build_workload(w)
+        M = len(w["sigma"])
+        sim = oracle.Sim(w["shape"], w["periodic"], M, openmp=True)
+        sim.set_geometry(a["solid"])
+        for k in range(M):
+            sim.set_species(k, w["sigma"][k], w["tau"][k])
+            sim.set_potential(k, a["V"][k])
+            sim.set_body_force(k, w["body"][k])
+        sim.set_wall_potential(a["phi"], a["amp"])
+        for k in range(M):
+            sim.init_density(k, a["n"][k])
+        sim.step(1)
+        t0 = time.perf_counter()
+        sim.step(steps)
+        dt = time.perf_counter() - t0
+        N = int(np.prod(w["shape"]))
+        out[name] = {"steps": steps, "s_per_step": dt / steps, "mlups_per_species": N * M * steps / dt / 1e6}
+        sim.close()
+    return out
 
 
 def run_reference(args):
@@ -284,8 +353,8 @@ def run_reference(args):
     w = inputs.WORKLOADS[args.workload]()
     w["name"] = args.workload
     arrays = inputs.build_workload(w)
-    L = 24 if w["kind"] == "well" else 20
-    sim, nodes = oracle_sample_sim(w, arrays, L)
+    L = 32
+    sim, nodes = oracle_sample_sim(w, arrays, L, openmp=True)
     M = len(w["sigma"])
     for _ in range(args.warmup):
         sim.step(1)
@@ -294,12 +363,14 @@ def run_reference(args):
         sim.step(1)
     dt = time.perf_counter() - t0
     value = nodes * M * args.steps / dt / 1e6
-    sample = "each step is one FP64 oracle step of %s" % sample_text(w, L)
+    sample = "each step is one FP64 oracle step of %s (OpenMP build, %d threads)" % (sample_text(w, L),
+                                                                                    oracle_threads())
     line = {"impl": "reference", "metric": "Enskog-LB MLUPS/species", "value": value, "unit": "MLUPS/species",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload + ": " + WORKLOAD_TEXT.get(args.workload, ""), "sample": sample},
-            "cpu_baseline": {"value": value, "unit": "MLUPS/species", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MLUPS/species", "cores": oracle_threads(), "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": "MLUPS/species", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -342,32 +413,85 @@ def fft_size(n):
         m += 1
 
 
-def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof):
-    """Each stage kernel against its own bound, from the live per-stage event times.  Algorithmic bytes
-    per launch: K1 reads 19 f~ and writes one padded density per node and species; K4 reads and writes
-    f~ and g~ (76 populations) per node and species; K2 reads the padded densities and writes g and g n
-    of every ordered pair.  K3 is the roofline of the dominant-kernel entry when it dominates."""
+def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_method):
+    """Each stage kernel against its own bound, from the live per-stage event times.
+    K1 (HBM): reads 19 f~ and writes one padded density per node and species.
+    K4: reads and writes f~ and g~ (76 populations) per node and species; HBM bound with 32- and 16-bit
+    storage; with FP64 storage it is bound by GB300's FP64 rate, so it also carries the FP64-rate roofline
+    of K4_FLOPS_PER_NODE_SPECIES flops per node and species against the nominal FP64 rate.
+    K2, stencil form: sum_b |B_b| shared-memory loads of the padded densities per node, against the
+    shared-memory load bandwidth (32 banks x 4 B per clock per SM); in spectral form its fields through
+    HBM.  K3 is the roofline of the dominant-kernel entry when it dominates."""
     rb = 8 if prec == "fp64" else 4
-    alg = {"density": N * M * (QPOP * sb + rb),
-           "collide": N * M * 4 * QPOP * sb,
-           "contact": N * (M * rb + 2 * M * M * rb)}
     out = {}
-    for k, b in alg.items():
-        if k not in stages or stages[k][1] == 0:
-            continue
-        t = stages[k][0] / stages[k][1] * 1e-3
-        out[k] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
-                  "achieved_gbs": b / t / 1e9, "frac_of_measured_hbm": b / t / 1e9 / hbm}
+
+    def t_of(k):
+        return stages[k][0] / stages[k][1] * 1e-3 if k in stages and stages[k][1] else None
+
+    t = t_of("density")
+    if t:
+        b = N * M * (QPOP * sb + rb)
+        out["density"] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
+                          "achieved_gbs": b / t / 1e9, "peak_gbs": hbm, "frac": b / t / 1e9 / hbm,
+                          "frac_of_measured_hbm": b / t / 1e9 / hbm}
+    t = t_of("collide")
+    if t:
+        b = N * M * 4 * QPOP * sb
+        e = {"algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3, "achieved_gbs": b / t / 1e9,
+             "frac_of_measured_hbm": b / t / 1e9 / hbm}
+        if prec == "fp64":
+            fl = N * M * K4_FLOPS_PER_NODE_SPECIES
+            e.update({"bound": "alu", "algorithmic_flops_per_launch": fl, "achieved_tflops": fl / t / 1e12,
+                      "peak_tflops": FP64_NOMINAL_TFLOPS, "frac": fl / t / 1e12 / FP64_NOMINAL_TFLOPS,
+                      "peak_source": "FP64 nominal vector rate of GB300 (%.2f TFLOP/s); flops per node and "
+                                     "species counted from the source: %d" % (FP64_NOMINAL_TFLOPS,
+                                                                              K4_FLOPS_PER_NODE_SPECIES)})
+        else:
+            e.update({"bound": "hbm", "peak_gbs": hbm, "frac": b / t / 1e9 / hbm})
+        out["collide"] = e
+    t = t_of("contact")
+    if t:
+        if shell_method == "direct":
+            loads = sum(ball_count(0.5 * s) for s in w["sigma"] if s > 0)
+            b = N * loads * rb
+            peak = sms * SMEM_BYTES_PER_CLK_PER_SM * clk * 1e6 / 1e9
+            out["contact"] = {"bound": "smem", "algorithmic_smem_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
+                              "achieved_gbs": b / t / 1e9, "peak_gbs": peak, "frac": b / t / 1e9 / peak,
+                              "peak_source": "shared-memory loads: %d SMs x 128 B/clock x %.0f MHz" % (sms, clk),
+                              "note": "ball sums from a TMA-staged ring: %d shared loads per node" % loads}
+        else:
+            # spectral contact stage: M densities embedded and transformed forward, ball spectra applied,
+            # M inverse transforms, then the pointwise contact kernel (ball averages in, g and g n out)
+            L = spectral_grid(w)
+            Lr, Lc = L[0] * L[1] * L[2], (L[0] // 2 + 1) * L[1] * L[2]
+            b = (M * (rb * N + rb * Lr)                     # embed: n in, grid out
+                 + M * (rb * Lr + 2 * rb * Lc)              # forward transforms
+                 + M * 4 * rb * Lc                          # ball multiply: spectrum in and out
+                 + M * (2 * rb * Lc + rb * Lr)              # inverse transforms
+                 + M * rb * Lr + M * M * rb * (N + Lr))     # contact: averages in; g_ab, g_ab n_b out
+            out["contact"] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
+                              "achieved_gbs": b / t / 1e9, "peak_gbs": hbm, "frac": b / t / 1e9 / hbm,
+                              "frac_of_measured_hbm": b / t / 1e9 / hbm, "fft_grid": L}
     if "shell" in stages and roof.get("bound") == "alu":
         out["shell"] = {"bound": "alu", "achieved_tflops": roof["achieved"], "frac": roof["frac"]}
     return out
 
 
-def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_kind, sampler=None):
+def spectral_grid(w):
+    """Grid of the spectral form: the lattice along periodic axes, the next 2-3-5-7 size of at least
+    n + S_max along closed ones (S_max the largest pair diameter)."""
+    M = len(w["sigma"])
+    S_max = max(int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M))
+    return [n if per else fft_size(n + S_max) for n, per in zip(w["shape"], w["periodic"])]
+
+
+def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_kind, sampler=None, sms=None):
     """Time `steps` DD-TR steps of workload wname after `warmup` untimed ones; per-stage device times from
     CUDA events on the launching stream; returns the result fields and the input arrays."""
     import torch
     from paper_1202_3842_gb300 import inputs
+    if sms is None:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
     w = inputs.WORKLOADS[wname]()
     w["name"] = wname
     arrays = inputs.build_workload(w)
@@ -435,8 +559,7 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
         # flops per real transform (half a complex transform of that size).  FP32: bound by HBM, counted
         # as one read and one write of every transformed field plus the pointwise kernels' fields, each
         # touched once.
-        S_max = max(int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M))
-        L = [n if per else fft_size(n + S_max) for n, per in zip(w["shape"], w["periodic"])]
+        L = spectral_grid(w)
         Lr = L[0] * L[1] * L[2]
         Lc = (L[0] // 2 + 1) * L[1] * L[2]
         nf, ni, nS = M * M, 3 * M * M + 3 * M, len(set(S for S in [
@@ -464,15 +587,17 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
         per_launch_flops = flops / len(S_list)
         achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
         clk = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = SMS * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12 if prec != "fp64" else None
+        peak = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12 if prec != "fp64" else None
         roof = {"kernel": "k_shell_force (K3 mean-field shell force)", "bound": "alu", "achieved": achieved,
                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                 "traffic": traffic_for("shell", wname, prec), "algorithmic_flops_per_launch": per_launch_flops,
                 "launches": dom_n, "avg_launch_ms": per_launch_ms,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock)" % clk}
+                "peak_source": "FP32 FMA: %d SMs (the device's multiprocessor count) x 128 lanes x 2 flop x "
+                               "%.0f MHz (max SM clock)" % (sms, clk)}
     step_bytes = N * M * 4 * QPOP * sb
     hbm = float(peaks["hbm_gbs"])
-    res_kernels = kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof)
+    res_kernels = kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms,
+                                   float(peaks.get("sm_max_mhz", 2070.0)), shell_method)
     res = {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
            "mlups_nodes": value / M,
            "config": {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "nodes": N,
@@ -484,7 +609,7 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
            "population_gbs_whole_step": step_bytes / (ms_step * 1e-3) / 1e9,
            "population_gbs_whole_step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
            "kernels": res_kernels,
-           "gpu_launches": launches, "state_after": state,
+           "gpu_launches": launches, "state_after": state, "sm_count": sms,
            "max_u_over_vT_after": umax / math.sqrt(1.0 / 3.0)}
     if clocks is not None:
         res["clocks"] = clocks
@@ -636,6 +761,9 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if args.cpu_study:
+        print(json.dumps({"cpu_oracle_openmp": cpu_study()}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-_LIB = None
+_LIBS = {}
 
 _c_int_p = ctypes.POINTER(ctypes.c_int)
 _c_dbl_p = ctypes.POINTER(ctypes.c_double)
@@ -25,11 +25,12 @@ _c_u32_p = ctypes.POINTER(ctypes.c_uint32)
 _c_long_p = ctypes.POINTER(ctypes.c_long)
 
 
-def lib():
-    """Load (building first if needed) the oracle shared library."""
-    global _LIB
-    if _LIB is None:
-        path = _build.build()
+def lib(openmp=False):
+    """Load (building first if needed) the oracle shared library: the single-threaded parity build, or with
+    openmp=True the OpenMP build of the same source used to time the CPU baseline on all host cores."""
+    key = bool(openmp)
+    if key not in _LIBS:
+        path = _build.build(openmp=key)
         L = ctypes.CDLL(path)
         L.or_lattice.argtypes = [_c_int_p, _c_dbl_p, _c_int_p]
         L.or_shell.argtypes = [ctypes.c_double, _c_int_p, ctypes.c_int]
@@ -71,8 +72,8 @@ def lib():
         L.or_get_flux.argtypes = [ctypes.c_void_p, _c_dbl_p, _c_long_p]
         L.or_steps_done.argtypes = [ctypes.c_void_p]
         L.or_steps_done.restype = ctypes.c_long
-        _LIB = L
-    return _LIB
+        _LIBS[key] = L
+    return _LIBS[key]
 
 
 def _p(a, ctype):
@@ -217,18 +218,19 @@ def quasipressure(shape, periodic, sigma, n, V, gbody, solid=None):
 class Sim:
     """Oracle simulation: the same sequence of set-up calls as the library."""
 
-    def __init__(self, shape, periodic=(1, 1, 1), nspecies=1):
+    def __init__(self, shape, periodic=(1, 1, 1), nspecies=1, openmp=False):
+        self._L = lib(openmp)
         self.shape = tuple(int(v) for v in shape)
         self.N = self.shape[0] * self.shape[1] * self.shape[2]
         self.M = int(nspecies)
         per = [int(bool(v)) for v in periodic]
-        self._h = lib().or_create(*self.shape, *per, self.M)
+        self._h = self._L.or_create(*self.shape, *per, self.M)
         if not self._h:
             raise ValueError("oracle: bad sizes")
 
     def close(self):
         if self._h:
-            lib().or_destroy(self._h)
+            self._L.or_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -239,73 +241,76 @@ class Sim:
 
     def set_geometry(self, solid):
         s = _solid(solid, self.N)
-        lib().or_set_solid(self._h, _p(s, ctypes.c_uint8))
+        self._L.or_set_solid(self._h, _p(s, ctypes.c_uint8))
 
     def set_species(self, s, sigma, tau):
-        if lib().or_set_species(self._h, s, float(sigma), float(tau)) != 0:
+        if self._L.or_set_species(self._h, s, float(sigma), float(tau)) != 0:
             raise ValueError("oracle: bad species parameters")
 
     def set_potential(self, s, V):
         V = _dbl(V).reshape(self.N)
-        lib().or_set_potential(self._h, s, _p(V, ctypes.c_double))
+        self._L.or_set_potential(self._h, s, _p(V, ctypes.c_double))
 
     def set_wall_potential(self, phi, amp):
         phi = _dbl(phi).reshape(self.N)
         amp = _dbl(amp).reshape(self.N)
-        lib().or_set_wall_potential(self._h, _p(phi, ctypes.c_double), _p(amp, ctypes.c_double))
+        self._L.or_set_wall_potential(self._h, _p(phi, ctypes.c_double), _p(amp, ctypes.c_double))
 
     def set_body_force(self, s, g):
         g = _dbl(g)
-        lib().or_set_body_force(self._h, s, _p(g, ctypes.c_double))
+        self._L.or_set_body_force(self._h, s, _p(g, ctypes.c_double))
 
     def set_consistent_moments(self, on):
-        lib().or_set_consistent_moments(self._h, int(bool(on)))
+        """0 (or False): the moments as printed; 1 (or True): the map g = g~ + Omega/2 applied to the printed S_g;
+        2: that map with the d Pi/d n term of S_g added (Sec. "Stabilization")."""
+        if self._L.or_set_consistent_moments(self._h, int(on)) != 0:
+            raise ValueError("consistent_moments must be 0, 1 or 2")
 
     def set_visc(self, on):
-        if lib().or_set_visc(self._h, int(bool(on))) != 0:
+        if self._L.or_set_visc(self._h, int(bool(on))) != 0:
             raise ValueError("C^visc needs the DD-TR scheme")
 
     def set_scheme(self, scheme):
         """0 DD-TR (default), 1 SD-TR, 2 SD-EU, 3 DD-EU (Sec. "Results": single or double distribution,
         Euler or trapezoidal integration)."""
-        if lib().or_set_scheme(self._h, int(scheme)) != 0:
+        if self._L.or_set_scheme(self._h, int(scheme)) != 0:
             raise ValueError("unknown scheme %r" % (scheme,))
 
     def set_flux_plane(self, axis, plane):
-        lib().or_set_flux_plane(self._h, int(axis), int(plane))
+        self._L.or_set_flux_plane(self._h, int(axis), int(plane))
 
     def init_density(self, s, n):
         n = _dbl(n).reshape(self.N)
-        lib().or_init_density(self._h, s, _p(n, ctypes.c_double))
+        self._L.or_init_density(self._h, s, _p(n, ctypes.c_double))
 
     def set_populations(self, s, f, g):
         f = _dbl(f).reshape(19, self.N)
         g = _dbl(g).reshape(19, self.N)
-        lib().or_set_populations(self._h, s, _p(f, ctypes.c_double), _p(g, ctypes.c_double))
+        self._L.or_set_populations(self._h, s, _p(f, ctypes.c_double), _p(g, ctypes.c_double))
 
     def get_populations(self, s):
         f = np.zeros((19, self.N))
         g = np.zeros((19, self.N))
-        lib().or_get_populations(self._h, s, _p(f, ctypes.c_double), _p(g, ctypes.c_double))
+        self._L.or_get_populations(self._h, s, _p(f, ctypes.c_double), _p(g, ctypes.c_double))
         return f, g
 
     def step(self, nsteps=1):
-        lib().or_step(self._h, int(nsteps))
+        self._L.or_step(self._h, int(nsteps))
 
     def observe(self):
         """dict of n [M,N], J [M,3,N], C [M,3,N], Pi [M,N], F [M,3,N], g [M,M,N] of the current state."""
         M, N = self.M, self.N
         out = dict(n=np.zeros((M, N)), J=np.zeros((M, 3, N)), C=np.zeros((M, 3, N)), Pi=np.zeros((M, N)),
                    F=np.zeros((M, 3, N)), g=np.zeros((M, M, N)))
-        lib().or_observe(self._h, *[_p(out[k], ctypes.c_double) for k in ("n", "J", "C", "Pi", "F", "g")])
+        self._L.or_observe(self._h, *[_p(out[k], ctypes.c_double) for k in ("n", "J", "C", "Pi", "F", "g")])
         return out
 
     def flux(self):
         """(per-species running flux sum [M], number of steps accumulated)."""
         s = np.zeros(self.M)
         c = ctypes.c_long(0)
-        lib().or_get_flux(self._h, _p(s, ctypes.c_double), ctypes.byref(c))
+        self._L.or_get_flux(self._h, _p(s, ctypes.c_double), ctypes.byref(c))
         return s, c.value
 
     def steps_done(self):
-        return lib().or_steps_done(self._h)
+        return self._L.or_steps_done(self._h)

@@ -34,7 +34,9 @@
  *              to the printed S_g: J = J~ + (h/2)(C^visc + nF),
  *              Pi = Pi~ + (h/2) beta C^mf . u^alpha (an ablation; it diverges
  *              on strongly compressed starts because the dropped d Pi/d n
- *              term of S_g is then not small).
+ *              term of S_g is then not small).  consistent_moments = 2 adds
+ *              that term (see dpi_dn_term): an exact, relaxation-time
+ *              independent rest state, stable only at low packing.
  *   S_g      : the coefficient of H2 in the C^mf term is 4, as printed.
  *   schemes  : (Sec. "Results") DD-TR is the default; the ablations are
  *              SD-TR: one distribution f, S = S_f with the whole force, and the
@@ -48,12 +50,24 @@
  *              is kept equal to f.
  *   force    : F = -grad_h V + g with the isotropic D3Q19 gradient.
  *   init     : f~ = g~ = w_p n(r,0) on fluid nodes, zero on solid nodes.
- *   C^visc   : not in this oracle (disabled in the hot path).
+ *   C^visc   : opt-in (or_set_visc): the viscous Enskog force of the Appendix
+ *              on the lattice shell, taken at the tilde velocities J~/n and
+ *              added where n F enters (J, S_f, S_g); off by default.
  */
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* The per-node loops carry OR_PARALLEL_FOR.  The parity build (no -fopenmp)
+ * ignores it and runs one thread; the timing build of the same source
+ * (-fopenmp) spreads those loops over the host cores.  Every node's arithmetic
+ * is the same either way, and the reductions (the plane flux) stay serial. */
+#ifdef _OPENMP
+#define OR_PARALLEL_FOR _Pragma("omp parallel for schedule(static)")
+#else
+#define OR_PARALLEL_FOR
+#endif
 
 #define Q 19
 #define MAXS 4
@@ -236,38 +250,57 @@ double or_bmcsl(double sa, double sb, double xi2, double xi3) {
     return 1.0 / one + 3.0 * s * xi2 / (one * one) + 2.0 * s * s * xi2 * xi2 / (one * one * one);
 }
 
+/* xi2 = (pi/6) sum_b sigma_b^2 nbar_b and xi3 = (pi/6) sum_b sigma_b^3 nbar_b of
+ * every node [N], with nbar_b the average of n_b over the ball B_{sigma_b/2}
+ * (zero density on solid nodes and outside non-periodic axes). */
+static void contact_xi(const grid_t *g, const uint8_t *solid, int M, const double *sigma, const double *n,
+                       double *xi2, double *xi3) {
+    long N = nsites(g);
+    int cap = 8192;
+    int *ball = (int *)malloc(sizeof(int) * 3 * cap);
+    double *nbar = (double *)calloc((size_t)M * N, sizeof(double));
+    for (int b = 0; b < M; ++b) {
+        int kb = or_ball(0.5 * sigma[b], ball, cap);
+        OR_PARALLEL_FOR
+        for (long i = 0; i < N; ++i) {
+            int x, y, z;
+            coords(g, i, &x, &y, &z);
+            double acc = 0.0;
+            for (int t = 0; t < kb; ++t)
+                acc += field_at(g, solid, n + (long)b * N, x + ball[3 * t], y + ball[3 * t + 1], z + ball[3 * t + 2]);
+            nbar[(long)b * N + i] = acc / kb;
+        }
+    }
+    OR_PARALLEL_FOR
+    for (long i = 0; i < N; ++i) {
+        double s2 = 0.0, s3 = 0.0;
+        for (int b = 0; b < M; ++b) {
+            s2 += (PI / 6.0) * sigma[b] * sigma[b] * nbar[(long)b * N + i];
+            s3 += (PI / 6.0) * sigma[b] * sigma[b] * sigma[b] * nbar[(long)b * N + i];
+        }
+        xi2[i] = s2;
+        xi3[i] = s3;
+    }
+    free(nbar);
+    free(ball);
+}
+
 /* g_ab(r) for every node and ordered pair: gpair[(a*M + b)*N + i].
  * n is [M][N]; the densities are ball-averaged over B_{sigma_b/2}. */
 void or_contact_values(int nx, int ny, int nz, const int *per, const uint8_t *solid, int M,
                        const double *sigma, const double *n, double *gpair) {
     grid_t g = {{nx, ny, nz}, {per[0], per[1], per[2]}};
     long N = nsites(&g);
-    int cap = 8192;
-    int *ball = (int *)malloc(sizeof(int) * 3 * cap);
-    double *nbar = (double *)calloc((size_t)M * N, sizeof(double));
-    for (int b = 0; b < M; ++b) {
-        int kb = or_ball(0.5 * sigma[b], ball, cap);
-        for (long i = 0; i < N; ++i) {
-            int x, y, z;
-            coords(&g, i, &x, &y, &z);
-            double acc = 0.0;
-            for (int t = 0; t < kb; ++t)
-                acc += field_at(&g, solid, n + (long)b * N, x + ball[3 * t], y + ball[3 * t + 1], z + ball[3 * t + 2]);
-            nbar[(long)b * N + i] = acc / kb;
-        }
-    }
-    for (long i = 0; i < N; ++i) {
-        double xi2 = 0.0, xi3 = 0.0;
-        for (int b = 0; b < M; ++b) {
-            xi2 += (PI / 6.0) * sigma[b] * sigma[b] * nbar[(long)b * N + i];
-            xi3 += (PI / 6.0) * sigma[b] * sigma[b] * sigma[b] * nbar[(long)b * N + i];
-        }
+    double *xi2 = (double *)malloc(sizeof(double) * N);
+    double *xi3 = (double *)malloc(sizeof(double) * N);
+    contact_xi(&g, solid, M, sigma, n, xi2, xi3);
+    OR_PARALLEL_FOR
+    for (long i = 0; i < N; ++i)
         for (int a = 0; a < M; ++a)
             for (int b = 0; b < M; ++b)
-                gpair[((long)a * M + b) * N + i] = or_bmcsl(sigma[a], sigma[b], xi2, xi3);
-    }
-    free(nbar);
-    free(ball);
+                gpair[((long)a * M + b) * N + i] = or_bmcsl(sigma[a], sigma[b], xi2[i], xi3[i]);
+    free(xi2);
+    free(xi3);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -291,6 +324,7 @@ void or_shell_force(int nx, int ny, int nz, const int *per, const uint8_t *solid
             double wab = or_shell_weight(sab);
             const double *gab = gpair + ((long)a * M + b) * N;
             const double *nb = n + (long)b * N;
+            OR_PARALLEL_FOR
             for (long i = 0; i < N; ++i) {
                 int x, y, z;
                 coords(&g, i, &x, &y, &z);
@@ -337,6 +371,7 @@ void or_visc_force(int nx, int ny, int nz, const int *per, const uint8_t *solid,
             const double *gab = gpair + ((long)a * M + b) * N;
             const double *nb = n + (long)b * N;
             const double *ub = u + (long)b * 3 * N;
+            OR_PARALLEL_FOR
             for (long i = 0; i < N; ++i) {
                 int x, y, z;
                 coords(&g, i, &x, &y, &z);
@@ -367,6 +402,7 @@ void or_visc_force(int nx, int ny, int nz, const int *per, const uint8_t *solid,
 void or_force_field(int nx, int ny, int nz, const int *per, const double *V, const double *gbody, double *F) {
     grid_t g = {{nx, ny, nz}, {per[0], per[1], per[2]}};
     long N = nsites(&g);
+    OR_PARALLEL_FOR
     for (long i = 0; i < N; ++i) {
         int x, y, z;
         coords(&g, i, &x, &y, &z);
@@ -438,7 +474,7 @@ typedef struct {
     int M;
     double sigma[MAXS], tau[MAXS];
     double gbody[MAXS][3];
-    int consistent_moments;
+    int consistent_moments;  /* 0 printed, 1 map-consistent, 2 map-consistent with the d Pi/d n term */
     int visc;            /* 1: add C^{visc} of the tilde velocities to the force terms */
     int scheme;          /* 0 DD-TR, 1 SD-TR, 2 SD-EU, 3 DD-EU */
     uint8_t *solid;      /* [N] */
@@ -449,6 +485,9 @@ typedef struct {
     /* per-step work fields */
     double *n, *gpair, *Cmf, *F, *J, *Pi;
     double *Cvisc, *ut;  /* C^{visc} [M][3][N] and the tilde velocities J~/n [M][3][N] */
+    double *sD;          /* [M][N] zeroth moment of the d Pi/d n term of S_g (consistent_moments = 2) */
+    double *nh1, *nh2;   /* [M][N] densities of the two previous steps, for that term */
+    int nhist;           /* how many of nh1, nh2 hold a density */
     int flux_axis, flux_plane;
     double flux_sum[MAXS];
     long flux_count;
@@ -480,6 +519,9 @@ or_sim *or_create(int nx, int ny, int nz, int px, int py, int pz, int M) {
     s->Pi = (double *)calloc((size_t)M * N, sizeof(double));
     s->Cvisc = (double *)calloc((size_t)M * 3 * N, sizeof(double));
     s->ut = (double *)calloc((size_t)M * 3 * N, sizeof(double));
+    s->sD = (double *)calloc((size_t)M * N, sizeof(double));
+    s->nh1 = (double *)calloc((size_t)M * N, sizeof(double));
+    s->nh2 = (double *)calloc((size_t)M * N, sizeof(double));
     s->flux_axis = 0;
     s->flux_plane = -1;
     return s;
@@ -491,6 +533,7 @@ void or_destroy(or_sim *s) {
     free(s->f); free(s->gd); free(s->fpost); free(s->gpost);
     free(s->n); free(s->gpair); free(s->Cmf); free(s->F); free(s->J); free(s->Pi);
     free(s->Cvisc); free(s->ut);
+    free(s->sD); free(s->nh1); free(s->nh2);
     free(s);
 }
 
@@ -525,6 +568,7 @@ int or_set_body_force(or_sim *s, int a, const double *g3) {
 }
 
 int or_set_consistent_moments(or_sim *s, int on) {
+    if (on < 0 || on > 2) return -1;
     s->consistent_moments = on;
     return 0;
 }
@@ -561,6 +605,7 @@ int or_set_flux_plane(or_sim *s, int axis, int plane) {
 int or_init_density(or_sim *s, int a, const double *n0) {
     if (a < 0 || a >= s->M) return -1;
     long N = s->N;
+    s->nhist = 0;
     for (int p = 0; p < Q; ++p)
         for (long i = 0; i < N; ++i) {
             double v = s->solid[i] ? 0.0 : weight_of(p) * n0[i];
@@ -572,6 +617,7 @@ int or_init_density(or_sim *s, int a, const double *n0) {
 
 int or_set_populations(or_sim *s, int a, const double *f, const double *g) {
     if (a < 0 || a >= s->M) return -1;
+    s->nhist = 0;
     memcpy(s->f + (long)a * Q * s->N, f, sizeof(double) * Q * s->N);
     memcpy(s->gd + (long)a * Q * s->N, g, sizeof(double) * Q * s->N);
     return 0;
@@ -595,6 +641,101 @@ static void compute_forces(or_sim *s) {
     free(Vt);
 }
 
+/* The d Pi/d n term of S_g (Sec. "Stabilization", evolution equation of g):
+ *   -sum_b (d Pi^a/d n^b - delta_ab) (div(n^b u^b) - u . grad n^b) Gamma_0,
+ * which the paper's discrete S_g drops.  With div(n^b u^b) = -d n^b/dt the
+ * bracket is minus the material derivative D n^b = dn^b/dt + u . grad n^b, so
+ * the term is  sum_b A_ab D n^b Gamma_0  with A_ab = d Pi^a/d n^b - delta_ab.
+ * Readings (the paper leaves them open):
+ *   - A_ab in the local limit of the quasi-pressure: grad(Pi^a - n^a) =
+ *     -beta C^a, and the lattice shell force of a slowly varying density is
+ *     C^a = -kT n^a sum_b (4 pi/3) s_ab^3 [g_ab grad n^b + n^b grad g_ab / 2]
+ *     (s_ab the pair diameter; the linear-ramp identity of the shell weight and
+ *     the endpoint average of g), so
+ *       A_ab = n^a [(4 pi/3) s_ab^3 g_ab
+ *                   + sum_c (2 pi/3) s_ac^3 n^c (d g_ac/d xi2 dxi2/dn^b + d g_ac/d xi3 dxi3/dn^b)],
+ *     dxi_k/dn^b = (pi/6) sigma_b^k, the BMCSL derivatives at the node's xi;
+ *   - the mixture equation prints n^b before (d Pi^a/d n^b - delta_ab); the
+ *     one-component equation and the equation for D(Pi - n)/Dt it comes from
+ *     have no such factor, so it is not applied;
+ *   - D n^b over the step [t, t+1] the trapezoidal rule integrates: the
+ *     increment n(t+1) - n(t) by second-order extrapolation of the last two,
+ *     (3/2)(n(t) - n(t-1)) - (1/2)(n(t-1) - n(t-2)) (n(t) - n(t-1) after one
+ *     step, 0 at the first), plus u . grad_h n^b with the isotropic D3Q19
+ *     gradient (a solid or outside neighbour contributes n^b(r));
+ *   - Gamma_0 projects onto w_p (its higher Hermite moments vanish), so the
+ *     term adds w_p s^a to S_g and s^a to its zeroth moment.
+ * Fills s->sD [M][N] and adds s^a/2 to Pi^a (the map g = g~ + h Omega/2). */
+static void bmcsl_derivatives(double sa, double sb, double xi2, double xi3, double *g, double *d2, double *d3) {
+    double s = (sa + sb > 0.0) ? sa * sb / (sa + sb) : 0.0;
+    double o = 1.0 - xi3;
+    *g = 1.0 / o + 3.0 * s * xi2 / (o * o) + 2.0 * s * s * xi2 * xi2 / (o * o * o);
+    *d2 = 3.0 * s / (o * o) + 4.0 * s * s * xi2 / (o * o * o);
+    *d3 = 1.0 / (o * o) + 6.0 * s * xi2 / (o * o * o) + 6.0 * s * s * xi2 * xi2 / (o * o * o * o);
+}
+
+static void dpi_dn_term(or_sim *s) {
+    long N = s->N;
+    int M = s->M;
+    double *xi2 = (double *)malloc(sizeof(double) * N), *xi3 = (double *)malloc(sizeof(double) * N);
+    contact_xi(&s->g, s->solid, M, s->sigma, s->n, xi2, xi3);
+    OR_PARALLEL_FOR
+    for (long i = 0; i < N; ++i) {
+        for (int a = 0; a < M; ++a) s->sD[(long)a * N + i] = 0.0;
+        if (s->solid[i]) continue;
+        int x, y, z;
+        coords(&s->g, i, &x, &y, &z);
+        double ntot = 0.0, Jtot[3] = {0.0, 0.0, 0.0};
+        for (int a = 0; a < M; ++a) {
+            ntot += s->n[(long)a * N + i];
+            for (int c = 0; c < 3; ++c) Jtot[c] += s->J[((long)a * 3 + c) * N + i];
+        }
+        double u[3];
+        for (int c = 0; c < 3; ++c) u[c] = ntot > 0.0 ? Jtot[c] / ntot : 0.0;
+        double Dn[MAXS];
+        for (int b = 0; b < M; ++b) {
+            const double *nb = s->n + (long)b * N;
+            double grad[3] = {0.0, 0.0, 0.0};
+            for (int p = 1; p < Q; ++p) {
+                long q = site(&s->g, x + CV[p][0], y + CV[p][1], z + CV[p][2]);
+                double v = (q < 0 || s->solid[q]) ? nb[i] : nb[q];
+                for (int c = 0; c < 3; ++c) grad[c] += weight_of(p) * CV[p][c] * v;
+            }
+            long k = (long)b * N + i;
+            double inc = 0.0;
+            if (s->nhist >= 2)
+                inc = 1.5 * (nb[i] - s->nh1[k]) - 0.5 * (s->nh1[k] - s->nh2[k]);
+            else if (s->nhist == 1)
+                inc = nb[i] - s->nh1[k];
+            Dn[b] = inc + (u[0] * grad[0] + u[1] * grad[1] + u[2] * grad[2]) / CS2;
+        }
+        for (int a = 0; a < M; ++a) {
+            double sum = 0.0;
+            for (int b = 0; b < M; ++b) {
+                double sab = 0.5 * (s->sigma[a] + s->sigma[b]);
+                if (!(sab > 0.0)) continue;
+                double gab, d2, d3;
+                bmcsl_derivatives(s->sigma[a], s->sigma[b], xi2[i], xi3[i], &gab, &d2, &d3);
+                double A = (4.0 * PI / 3.0) * sab * sab * sab * gab;
+                for (int c = 0; c < M; ++c) {
+                    double sac = 0.5 * (s->sigma[a] + s->sigma[c]);
+                    if (!(sac > 0.0)) continue;
+                    double gac, e2, e3;
+                    bmcsl_derivatives(s->sigma[a], s->sigma[c], xi2[i], xi3[i], &gac, &e2, &e3);
+                    double dg = (PI / 6.0) * (s->sigma[b] * s->sigma[b] * e2 +
+                                              s->sigma[b] * s->sigma[b] * s->sigma[b] * e3);
+                    A += (2.0 * PI / 3.0) * sac * sac * sac * s->n[(long)c * N + i] * dg;
+                }
+                sum += s->n[(long)a * N + i] * A * Dn[b];
+            }
+            s->sD[(long)a * N + i] = sum;
+            s->Pi[(long)a * N + i] += 0.5 * sum;
+        }
+    }
+    free(xi2);
+    free(xi3);
+}
+
 /* Moments of the streamed populations and the physical moments (Sec. "Hard
  * sphere fluid mixture", moment equations): n = sum f~, Pi~ = sum g~,
  * J~ = sum c g~, then J and Pi by the reading stated in the header.  The SD
@@ -605,6 +746,7 @@ static void compute_moments(or_sim *s) {
     int M = s->M;
     compute_forces(s);
     for (int a = 0; a < M; ++a)
+        OR_PARALLEL_FOR
         for (long i = 0; i < N; ++i) {
             double nn = 0.0;
             if (!s->solid[i])
@@ -616,6 +758,7 @@ static void compute_moments(or_sim *s) {
     if (s->visc) {
         /* C^{visc} of the tilde moments (the collision functional taken at M~): u~ = J~/n */
         for (int a = 0; a < M; ++a)
+            OR_PARALLEL_FOR
             for (long i = 0; i < N; ++i) {
                 double Jt[3] = {0.0, 0.0, 0.0};
                 double nn = s->n[(long)a * N + i];
@@ -628,6 +771,7 @@ static void compute_moments(or_sim *s) {
                       s->Cvisc);
     }
     for (int a = 0; a < M; ++a)
+        OR_PARALLEL_FOR
         for (long i = 0; i < N; ++i) {
             double Pit = 0.0, Jt[3] = {0.0, 0.0, 0.0};
             const double *mom = single_distribution(s) ? s->f : s->gd;
@@ -670,6 +814,10 @@ static void compute_moments(or_sim *s) {
             for (int c = 0; c < 3; ++c) s->J[((long)a * 3 + c) * N + i] = J[c];
             s->Pi[(long)a * N + i] = Pi;
         }
+    if (s->scheme == DD_TR && s->consistent_moments == 2)
+        dpi_dn_term(s);
+    else
+        for (long t = 0; t < (long)M * N; ++t) s->sD[t] = 0.0;
 }
 
 /* One DD-TR step (Sec. "Hard sphere fluid mixture", trapezoidal two-distribution
@@ -699,6 +847,7 @@ static void one_step(or_sim *s) {
         s->flux_count += 1;
     }
 
+    OR_PARALLEL_FOR
     for (long i = 0; i < N; ++i) {
         if (s->solid[i]) {
             for (int a = 0; a < M; ++a)
@@ -749,10 +898,12 @@ static void one_step(or_sim *s) {
                 double Sf = 0.0;
                 for (int c = 0; c < 3; ++c) Sf += (Cm[c] + nF[c]) * (H1[c] + 2.0 * H2u[c]);
                 Sf *= wp;
-                /* S_g = w_p { C^mf . [u^a / v_T^2 + 4 H2 . u^a] + n F . [H1 + 2 H2 . u^a] } */
+                /* S_g = w_p { C^mf . [u^a / v_T^2 + 4 H2 . u^a] + n F . [H1 + 2 H2 . u^a] + s^a },
+                 * s^a the d Pi/d n term where it is on (zero otherwise) */
                 double Sg = 0.0;
                 for (int c = 0; c < 3; ++c)
                     Sg += Cm[c] * (ua[c] / CS2 + 4.0 * H2u[c]) + nF[c] * (H1[c] + 2.0 * H2u[c]);
+                Sg += s->sD[(long)a * N + i];
                 Sg *= wp;
                 long k = ((long)a * Q + p) * N + i;
                 double ft = s->f[k], gt = s->gd[k];
@@ -768,8 +919,14 @@ static void one_step(or_sim *s) {
         }
     }
 
+    /* densities of this step and the one before, for the d Pi/d n term */
+    memcpy(s->nh2, s->nh1, sizeof(double) * M * N);
+    memcpy(s->nh1, s->n, sizeof(double) * M * N);
+    if (s->nhist < 2) s->nhist += 1;
+
     /* streaming f~(r, t+1) = f~*(r - c_p), mid-point bounce-back on blocked links */
     for (int a = 0; a < M; ++a)
+        OR_PARALLEL_FOR
         for (long i = 0; i < N; ++i) {
             int x, y, z;
             coords(&s->g, i, &x, &y, &z);

@@ -1,9 +1,10 @@
 """torch.autograd.Function around the discrete adjoint of the C ABI.
 
-FluxObjective.apply(amp, gshift, sim, n_init, nsteps, ckpt_every, axis, plane) returns the flux
-through a plane averaged over nsteps DD-TR steps started from the rest state of the densities
-n_init, as a function of the wall-potential amplitude amp [N] (V += amp * phi for every species,
-phi set on sim beforehand) and a body force gshift [3] added to every species' base body force.
+FluxObjective.apply(amp, gshift, sim, phi, gbody, n_init, nsteps, ckpt_every, axis, plane) returns
+the flux through a plane averaged over nsteps DD-TR steps started from the rest state of the
+densities n_init [M][N], as a function of the wall-potential amplitude amp [N] (V += amp * phi for
+every species, with the wall shape phi [N]) and a body force gshift [3] added to every species' base
+body force gbody [M][3].  sim is an lbe.Simulation with its geometry, species and potentials set.
 The forward pass runs lbe_adjoint_flux_gradient once (forward sweep with checkpoints plus the
 reverse sweep) and keeps the gradients; backward scales them by the incoming gradient.
 """

@@ -269,7 +269,8 @@ def visc(cases=("well48", "channel128", "well24"), steps=600, prec="fp32", check
                 res = {"stable_steps": done, "u": float(np.sqrt((u ** 2).sum(0)).max() / CS)}
             except lbe.LbeError as e:
                 res = {"diverged_by_step": done + check, "error": str(e)}
-            sim.close()
+            finally:
+                sim.close()
             out[name]["visc" if on else "plain"] = res
     return out
 

@@ -40,7 +40,7 @@ def test_ideal_gas_tr_current_below_euler():
         assert 0.5 < tr["n"] / eu["n"] < 2.0, (xi, tr, eu)
 
 
-def test_viscous_force_study_runs_and_the_dense_well_diverges_no_later_without_it():
+def test_viscous_force_study_runs_and_the_dense_well_diverges_no_later_with_it():
     from paper_1202_3842_gb300 import studies
     r = studies.visc(cases=("well48", "well24"), steps=200)
     assert set(r) == {"well48", "well24"}
