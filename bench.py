@@ -703,7 +703,8 @@ def run_ours(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
               "data": "synthetic (seeded inputs of the workload's shape and distribution)"}
     for k in ("config", "roofline", "mlups_nodes", "kernels", "stage_ms_per_step", "population_gbs_whole_step",
-              "population_gbs_whole_step_frac", "gpu_launches", "clocks", "state_after", "max_u_over_vT_after"):
+              "population_gbs_whole_step_frac", "gpu_launches", "clocks", "state_after", "max_u_over_vT_after",
+              "sm_count"):
         result[k] = core.get(k)
 
     # end to end through the C ABI with host buffers: the timed region holds the host->device copy of the

@@ -48,7 +48,8 @@ typedef enum {
     LBE_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed            */
     LBE_ERR_DIVERGED = 5,    /* device check found n < 0, a non-finite value,
                                 or a packing xi3 >= 1                        */
-    LBE_ERR_TIMEOUT = 6,     /* reserved: no call in this library waits      */
+    LBE_ERR_TIMEOUT = 6,     /* reserved: not returned by this library (a
+                                device wait that gives up is LBE_ERR_CUDA)   */
     LBE_ERR_STATE = 7        /* call out of order (e.g. step before species) */
 } lbe_status;
 
@@ -312,6 +313,20 @@ lbe_status lbe_get_stage_times(lbe_ctx *ctx, double *ms, long long *launches);
 
 /* Number of kernel launches this context has issued (all entry points). */
 lbe_status lbe_get_launch_count(lbe_ctx *ctx, long long *launches);
+
+/* Self-test of the device-side failure detector (no counterpart in the
+ * paper).  Every wait of the TMA kernels on a copy is bounded: after 2^24
+ * polls it sets a bit in the context's device error word and the kernel
+ * returns, so a copy that never completes cannot hang the GPU, and the next
+ * checking call reports LBE_ERR_CUDA.  This call launches one CTA that arms
+ * an mbarrier for 16 bytes that no copy will deliver (none is issued, so
+ * nothing is in flight) and waits on it with that same bounded wait, limited
+ * to `polls` polls (1 .. 2^24).  It returns what a kernel whose wait gave up
+ * makes every later checking call return: LBE_ERR_CUDA, with
+ * lbe_last_error() naming the TMA wait.  The error word stays set, so the
+ * context's state is no longer trusted; destroy it.  LBE_ERR_INVALID_ARG for
+ * polls out of range.  Synchronises the context stream. */
+lbe_status lbe_probe_wait_timeout(lbe_ctx *ctx, int polls);
 
 /* Species masses mass[M] = sum over the lattice of n^s of the current state,
  * like the mass of lbe_get_totals, but without allocating any device memory.

@@ -99,8 +99,7 @@ __global__ void __launch_bounds__(32 * TYB, 1)
                      T *__restrict__ lg_ab, int *err) {
     using Tl = ShellTileZ<T, S, TZ, TYB>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *base = smem_align128(smem_raw);
     T *ring = reinterpret_cast<T *>(base);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
     constexpr int SLOT = Tl::SLOT_BYTES / (int)sizeof(T);
@@ -239,8 +238,7 @@ __global__ void __launch_bounds__(32 * TYB, 1)
                       int *err) {
     using Tl = ShellTileZ2<S, TZ, TYB>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *base = smem_align128(smem_raw);
     const f2 *ring = reinterpret_cast<const f2 *>(base);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
     constexpr int SLOT = Tl::SLOT_BYTES / 8;

@@ -789,7 +789,8 @@ lbe_status check_error_word(lbe_ctx *c) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "read error word");
     CK(cudaStreamSynchronize(c->stream), "stream sync");
-    if (e & ERR_TMA_WAIT) return fail(c, LBE_ERR_CUDA, "a TMA wait in the shell kernel gave up");
+    if (e & ERR_TMA_WAIT)
+        return fail(c, LBE_ERR_CUDA, "a bounded TMA wait gave up: the copy it waited for did not complete");
     if (e & ERR_DENSITY) return fail(c, LBE_ERR_DIVERGED, "negative or non-finite density");
     if (e & ERR_PACKING) return fail(c, LBE_ERR_DIVERGED, "local packing xi3 >= 1 or non-finite contact value");
     return LBE_OK;
@@ -1886,6 +1887,15 @@ lbe_status lbe_get_mass_noalloc(lbe_ctx *c, double *mass) {
        "lbe_get_mass_noalloc: copy result");
     CK(cudaStreamSynchronize(c->stream), "lbe_get_mass_noalloc: stream sync");
     return LBE_OK;
+}
+
+lbe_status lbe_probe_wait_timeout(lbe_ctx *c, int polls) {
+    TRY(ready(c));
+    if (polls < 1 || (long long)polls > WAIT_POLLS)
+        return fail(c, LBE_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
+    CK(launch_wait_probe((int *)c->err.p, (long long)polls, c->stream), "wait probe launch");
+    c->launches += 1;
+    return check_error_word(c);
 }
 
 lbe_status lbe_get_launch_count(lbe_ctx *c, long long *launches) {

@@ -1,17 +1,18 @@
-// K4 for one or two species with species-parallel lanes: fused moments +
-// DD-TR collision + pull streaming (Sec. "Hard sphere fluid mixture in a
-// potential well"; the arithmetic is that of k_collide in lbe_kernels.cu).
+// K4 for one or two species: fused moments + DD-TR collision + pull
+// streaming (Sec. "Hard sphere fluid mixture in a potential well"; the
+// arithmetic is that of k_collide in lbe_kernels.cu).
 //
-// Two species: lanes 0-15 of a warp take species 0 and lanes 16-31 species 1
-// of the same 16 consecutive nodes.  Each thread pulls only its own species'
-// 38 populations and keeps them in registers, computes that species' moments,
-// and gets the partner species' n and J from lane ^ 16 by a shuffle to form the
-// barycentric velocity u = (J_0 + J_1)/(n_0 + n_1).  A warp's load of one
-// population is two 64-byte runs, whole 32-byte sectors.  Compared with one
-// thread per node holding both species, the live state per thread halves,
-// which lets three CTAs of 256 threads share an SM.  One species: one thread
-// per node, 32 consecutive nodes per warp, u = J/n.  K1 (the pulled density)
-// uses the same lane layout.
+// Two species: a CTA of 256 threads takes 128 consecutive nodes; warps 0-3
+// take species 0 and warps 4-7 species 1 of the same nodes, 32 consecutive
+// nodes per warp.  Each thread pulls only its own species' 38 populations and
+// keeps them in registers, computes that species' moments, and gets the
+// partner species' n and J through shared memory to form the barycentric
+// velocity u = (J_0 + J_1)/(n_0 + n_1).  A warp's load of one population is
+// one 128-byte run of one species' array (FP32), as in the one-species
+// kernel.  Compared with one thread per node holding both species, the live
+// state per thread halves, which lets three CTAs of 256 threads share an SM.
+// One species: one thread per node, 32 consecutive nodes per warp, u = J/n.
+// K1 (the pulled density) uses the same layout.
 #include <math.h>
 
 #include <utility>
@@ -31,10 +32,9 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     k_collide_pair(Grid g, const S *__restrict__ src, S *__restrict__ dst, const uint32_t *__restrict__ mask,
                    const T *__restrict__ C, const T *__restrict__ F, StepParams sp, double *__restrict__ flux_buf) {
     static_assert(M == 1 || M == 2, "one or two species");
-    const int lane = threadIdx.x & 31;
-    const int a = M == 2 ? lane >> 4 : 0;  // species of this thread
-    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x >> 5) * 16 + (lane & 15)
-                               : (long long)blockIdx.x * NTP + threadIdx.x;
+    const int a = M == 2 ? (int)(threadIdx.x >> 7) : 0;         // species of this thread
+    const int loc = M == 2 ? (int)(threadIdx.x & 127) : 0;      // node within the CTA's 128
+    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + loc : (long long)blockIdx.x * NTP + threadIdx.x;
     const bool valid = i < g.N;
     int x = 0, y = 0, z = 0;
     if (valid) node_xyz(g, i, x, y, z);
@@ -81,12 +81,17 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
         }
         Pi = sp.consistent ? Pit + (T)1.5 * Cu : Pit - (T)0.5 * Cu;
     }
-    // the partner species (lane ^ 16) of the same node; every lane takes part
+    // the partner species of the same node, through shared memory; every thread takes part
     T np = 0, Jp[3] = {0, 0, 0};
     if constexpr (M == 2) {
-        np = __shfl_xor_sync(0xffffffffu, n, 16);
+        __shared__ T xch[2][4][NTP / 2];
+        xch[a][0][loc] = n;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) Jp[c] = __shfl_xor_sync(0xffffffffu, J[c], 16);
+        for (int c = 0; c < 3; ++c) xch[a][c + 1][loc] = J[c];
+        __syncthreads();
+        np = xch[1 - a][0][loc];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Jp[c] = xch[1 - a][c + 1][loc];
     }
     if (on_plane)
         flux_buf[(long long)a * psize + plane_index(g, sp.flux_axis, x, y, z)] =
@@ -137,16 +142,15 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     }(std::make_integer_sequence<int, Q>{});
 }
 
-// K1 for one or two species with the same lane layout: n^a(r) = sum_p f~_p(r) pulled, 0 on solid nodes,
+// K1 for one or two species with the same thread layout: n^a(r) = sum_p f~_p(r) pulled, 0 on solid nodes,
 // into the padded stencil field with its periodic images (the arithmetic of k_density).
 template <typename S, typename T, int M, bool SOLID>
 __global__ void __launch_bounds__(NTP)
     k_density_pair(Grid g, const S *__restrict__ pop, const uint32_t *__restrict__ mask, double n00, double n01,
                    T *__restrict__ npad, int *err) {
     static_assert(M == 1 || M == 2, "one or two species");
-    const int lane = threadIdx.x & 31;
-    const int a = M == 2 ? lane >> 4 : 0;
-    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x >> 5) * 16 + (lane & 15)
+    const int a = M == 2 ? (int)(threadIdx.x >> 7) : 0;
+    const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x & 127)
                                : (long long)blockIdx.x * NTP + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;

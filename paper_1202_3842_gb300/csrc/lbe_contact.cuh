@@ -73,8 +73,7 @@ __global__ void __launch_bounds__(256)
                   const uint32_t *__restrict__ mask, T *__restrict__ ln, int *err) {
     using Tl = ContactTile<T, M, RB>;
     extern __shared__ unsigned char smem_raw[];
-    unsigned char *base = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    unsigned char *base = smem_align128(smem_raw);
     const T *ring = reinterpret_cast<const T *>(base);
     uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
     constexpr int SLOT = Tl::SLOT_BYTES / (int)sizeof(T);

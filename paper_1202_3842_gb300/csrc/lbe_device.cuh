@@ -134,6 +134,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// First 128-byte aligned byte of the dynamic shared memory `raw`.  The offset is added to the pointer
+// itself (not through an integer round trip), so every pointer derived from the result stays a
+// shared-memory pointer to the compiler and reads through it compile to shared-memory loads.
+__device__ __forceinline__ unsigned char *smem_align128(unsigned char *raw) {
+    return raw + ((128u - (smem_u32(raw) & 127u)) & 127u);
+}
+
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -159,13 +166,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err) {
-    for (long long it = 0; it < (1ll << 24); ++it) {
+// Bounded wait for the phase with the given parity to complete: at most `polls` try_wait polls (the
+// kernels use the default, 2^24), then ERR_TMA_WAIT is recorded and the caller gets false.
+constexpr long long WAIT_POLLS = 1ll << 24;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
+                                                  long long polls = WAIT_POLLS) {
+    for (long long it = 0; it < polls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
     }
     atomicOr(err, ERR_TMA_WAIT);
     return false;
+}
+
+__device__ __forceinline__ void mbar_inval(uint64_t *bar) {
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // 3-D tiled TMA load of one box into shared memory; completion is signalled on bar.

@@ -640,4 +640,24 @@ cudaError_t launch_velocity(int M, long long N, int s, const double *n, const do
     return cudaGetLastError();
 }
 
+// Self-test of the failure detector of the TMA kernels: one thread arms an mbarrier for 16 bytes that
+// no copy will deliver (none is issued, so nothing is in flight) and waits on it with the kernels'
+// bounded wait, limited to `polls` polls.  The wait gives up and records ERR_TMA_WAIT in the error
+// word, as a kernel whose copy never completed would; the barrier is invalidated before the CTA exits.
+__global__ void k_wait_probe(int *err, long long polls) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        mbar_arrive_expect_tx(&bar, 16u);
+        mbar_wait_bounded(&bar, 0u, err, polls);
+        mbar_inval(&bar);
+    }
+}
+
+cudaError_t launch_wait_probe(int *err, long long polls, cudaStream_t st) {
+    k_wait_probe<<<1, 32, 0, st>>>(err, polls);
+    return cudaGetLastError();
+}
+
 }  // namespace lbe

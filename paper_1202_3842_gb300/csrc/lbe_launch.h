@@ -80,6 +80,7 @@ struct ShellLaunch {
 
 // Geometry
 cudaError_t launch_link_mask(const Grid &g, const uint8_t *solid, uint32_t *mask, cudaStream_t st);
+cudaError_t launch_wait_probe(int *err, long long polls, cudaStream_t st);
 // Force field F^a = -grad_h (V^a + amp*phi) + g^a, stored as T [3][N].
 cudaError_t launch_force_field(Prec p, const Grid &g, const double *V, const double *phi, const double *amp,
                                const double gbody[3], void *F, cudaStream_t st);

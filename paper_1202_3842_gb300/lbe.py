@@ -84,6 +84,7 @@ def lib():
             "lbe_get_link_mask": [_P, ctypes.POINTER(ctypes.c_uint32)],
             "lbe_shell": [ctypes.c_double, _I, ctypes.c_int, _I],
             "lbe_get_launch_count": [_P, ctypes.POINTER(ctypes.c_longlong)],
+            "lbe_probe_wait_timeout": [_P, ctypes.c_int],
             "lbe_set_stage_timing": [_P, ctypes.c_int],
             "lbe_get_stage_times": [_P, _D, ctypes.POINTER(ctypes.c_longlong)],
             "lbe_get_mass_noalloc": [_P, _D],
@@ -348,6 +349,10 @@ def lbe_get_launch_count(ctx):
     v = ctypes.c_longlong(0)
     _check(lib().lbe_get_launch_count(ctx, ctypes.byref(v)), ctx)
     return v.value
+
+
+def lbe_probe_wait_timeout(ctx, polls):
+    _check(lib().lbe_probe_wait_timeout(ctx, int(polls)), ctx)
 
 
 def lbe_init_density_quasipressure(ctx, M, N, n):

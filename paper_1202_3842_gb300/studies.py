@@ -16,6 +16,8 @@ numbers; ``python -m paper_1202_3842_gb300.studies <study> [--quick]`` prints on
 - ``init``: the transient of the spurious current from the rest state and from the quasi-pressure
   state of the second distribution.
 - ``visc``: stability with and without the viscous Enskog force.
+- ``precision``: the storage precisions (FP32 and the shifted BF16 and FP16 forms) against FP64 on the
+  128x32x32 bottleneck channel: density, velocity and time-averaged flux after the same steps.
 
 Scheme names: ``dd_tr`` (the method, printed moment recovery), ``dd_tr_c`` (DD-TR with the
 map-consistent recovery), ``sd_tr``, ``sd_eu``, ``dd_eu``.
@@ -275,6 +277,55 @@ def visc(cases=("well48", "channel128", "well24"), steps=600, prec="fp32", check
     return out
 
 
+def precision(steps=1000, precs=("fp64", "fp32", "bf16", "fp16"), workload="channel128", plane=None,
+              keep_fields=False):
+    """Each storage precision against the FP64 run of the same workload and step count (the FP64 path
+    matches the FP64 oracle to 1e-12): for every precision, max over species and fluid nodes of
+    |n - n64| / max n64 ("n"), |u^a - u^a_64| / max |u^a_64| ("u", per-species velocities J/n), and
+    |flux - flux64| / |flux64| of the time-averaged plane flux, per species and summed ("flux",
+    "flux_species").  The FP64 run's own values are returned under "reference"; keep_fields adds the
+    fields of every run (n [M][N], J [M][3][N], time-averaged flux [M]) under "fields"."""
+    w = inputs.WORKLOADS[workload]()
+    arr = inputs.build_workload(w)
+    M = len(w["sigma"])
+    plane = w["shape"][0] // 2 if plane is None else plane
+    fluid = arr["solid"] == 0
+    runs = {}
+    for prec in precs:
+        sim = lbe.Simulation(w["shape"], w["periodic"], M, prec)
+        try:
+            sim.set_geometry(arr["solid"])
+            for a in range(M):
+                sim.set_species(a, w["sigma"][a], w["tau"][a])
+                sim.set_potential(a, arr["V"][a])
+                sim.set_body_force(a, w["body"][a])
+            for a in range(M):
+                sim.init_density(a, arr["n"][a])
+            sim.set_flux_plane(0, plane)
+            sim.step(steps)
+            runs[prec] = {"n": [sim.density(a) for a in range(M)], "u": [sim.velocity(a) for a in range(M)],
+                          "flux": [sim.flux(a)[1] for a in range(M)]}
+            if keep_fields:
+                runs[prec]["J"] = [sim.momentum(a) for a in range(M)]
+        finally:
+            sim.close()
+    ref = runs["fp64"]
+    out = {"workload": workload, "steps": steps, "flux_plane_x": plane,
+           "reference": {"flux_species": ref["flux"], "max_n": [float(ref["n"][a].max()) for a in range(M)],
+                         "max_u": [float(np.abs(ref["u"][a][:, fluid]).max()) for a in range(M)]}}
+    ftot = sum(ref["flux"])
+    for prec, r in runs.items():
+        out[prec] = {
+            "n": max(float(np.abs(r["n"][a] - ref["n"][a])[fluid].max() / ref["n"][a].max()) for a in range(M)),
+            "u": max(float(np.abs(r["u"][a] - ref["u"][a])[:, fluid].max() / np.abs(ref["u"][a][:, fluid]).max())
+                     for a in range(M)),
+            "flux_species": [abs(r["flux"][a] - ref["flux"][a]) / abs(ref["flux"][a]) for a in range(M)],
+            "flux": abs(sum(r["flux"]) - ftot) / abs(ftot)}
+    if keep_fields:
+        out["fields"] = {prec: {k: r[k] for k in ("n", "J", "flux")} for prec, r in runs.items()}
+    return out
+
+
 # Reduced sizes for a quick look (a few seconds each on one GPU).
 QUICK = {
     "spurious": dict(xis=(6,), steps=1000),
@@ -284,9 +335,10 @@ QUICK = {
     "divergence": dict(shape=(64, 32, 32), length=32, steps=1000),
     "init": dict(xis=(6,), steps=500),
     "visc": dict(cases=("well48", "well24"), steps=200),
+    "precision": dict(steps=200),
 }
 STUDIES = dict(spurious=spurious, mixture=mixture, stability=stability, ideal_gas=ideal_gas,
-               divergence=divergence, init=init, visc=visc)
+               divergence=divergence, init=init, visc=visc, precision=precision)
 
 
 def main(argv=None):

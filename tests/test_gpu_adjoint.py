@@ -164,3 +164,75 @@ def test_repeated_adjoint_calls_reuse_the_spectral_transpose():
         np.testing.assert_array_equal(other[1], first[1])
         np.testing.assert_array_equal(other[2], first[2])
     g.close()
+
+
+def _phi_fresh(w, arr, amp, gshift, T, axis, plane, prec="fp64"):
+    a2 = dict(arr)
+    a2["amp"] = amp
+    w2 = dict(w)
+    w2["body"] = [tuple(np.asarray(b) + gshift) for b in w["body"]]
+    g = setup_gpu(w2, a2, prec)
+    try:
+        g.set_flux_plane(axis, plane)
+        g.step(T)
+        return g.flux(-1)[1]
+    finally:
+        g.close()
+
+
+@pytest.fixture(scope="module")
+def full_size_adjoint():
+    """The adjoint channel at its full size (256x64x64, slit width 12 and length 32, sigma 4/6, packing
+    0.25, wall potential of amplitude 1 k_BT with a seeded +-15% spread), over T = 200 steps with
+    checkpoints every 20: the FP64 and FP32 gradients of the flux through x = 128."""
+    w = inputs.WORKLOADS["channel256adj"]()
+    arr = inputs.build_workload(w)
+    rng = np.random.default_rng(11)
+    arr["amp"] = arr["amp"] * (1.0 + 0.3 * (rng.random(arr["amp"].size) - 0.5))
+    T, K, axis, plane = 200, 20, 0, 128
+    out = {"w": w, "arr": arr, "T": T, "axis": axis, "plane": plane}
+    for prec in ("fp64", "fp32"):
+        g = setup_gpu(w, arr, prec)
+        out[prec] = g.adjoint_flux_gradient(T, K, axis, plane)
+        g.close()
+    return out
+
+
+def test_full_size_fp64_adjoint_matches_central_differences(full_size_adjoint):
+    """The benchmark spec: the adjoint within 1e-4 relative of central differences (h = 1e-4 of the parameter
+    scale), here on the full-size adjoint channel: four random directions over the wall nodes, four
+    single wall nodes and the body force g_x, each against two FP64 forward runs of the GPU."""
+    S = full_size_adjoint
+    w, arr, T, axis, plane = S["w"], S["arr"], S["T"], S["axis"], S["plane"]
+    Phi, dA, dG = S["fp64"]
+    rng = np.random.default_rng(5)
+    N = arr["amp"].size
+    wall = np.flatnonzero(arr["phi"] > 0)
+    dirs = [rng.standard_normal(N) * (arr["phi"] > 0) for _ in range(4)]
+    # single nodes: the largest gradient entry, and three spread over the wall list
+    for node in (int(np.argmax(np.abs(dA))), wall[len(wall) // 7], wall[len(wall) // 2], wall[-3]):
+        d = np.zeros(N)
+        d[node] = 1.0
+        dirs.append(d)
+    h = 1e-4 * KT
+    for d in dirs:
+        fd = (_phi_fresh(w, arr, arr["amp"] + h * d, np.zeros(3), T, axis, plane)
+              - _phi_fresh(w, arr, arr["amp"] - h * d, np.zeros(3), T, axis, plane)) / (2 * h)
+        ad = float(dA @ d)
+        assert abs(ad - fd) <= 1e-4 * max(abs(fd), 1e-3 * np.abs(dA).max()), (ad, fd)
+    hg = 1e-4 * w["body"][0][0]
+    e = np.array([hg, 0.0, 0.0])
+    fd = (_phi_fresh(w, arr, arr["amp"], e, T, axis, plane) - _phi_fresh(w, arr, arr["amp"], -e, T, axis, plane)) / (2 * hg)
+    assert abs(dG[0] - fd) <= 1e-4 * abs(fd), (dG[0], fd)
+
+
+def test_full_size_fp32_adjoint_against_fp64(full_size_adjoint):
+    """The FP32 adjoint on the same full-size case, against the FP64 adjoint (FP32 forward and adjoint
+    arithmetic over 200 steps): Phi within the benchmark spec's FP32 flux bound of 1e-3, the wall-amplitude
+    gradient within 1e-2 of its largest entry, dPhi/dg_x within 1e-3."""
+    Phi64, dA64, dG64 = full_size_adjoint["fp64"]
+    Phi32, dA32, dG32 = full_size_adjoint["fp32"]
+    err = {"Phi": abs(Phi32 - Phi64) / abs(Phi64), "dA": float(np.abs(dA32 - dA64).max() / np.abs(dA64).max()),
+           "dG": abs(dG32[0] - dG64[0]) / abs(dG64[0])}
+    print("full-size FP32 adjoint errors against FP64:", err)
+    assert err["Phi"] <= 1e-3 and err["dA"] <= 1e-2 and err["dG"] <= 1e-3, err
