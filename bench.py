@@ -654,11 +654,73 @@ def measure_adjoint(prec, wname="channel256adj", T=2000, K=100):
     sim.close()
     del sim
     torch.cuda.empty_cache()
+    fd = adjoint_fd_check(wname)
     return {"workload": wname + ": " + WORKLOAD_TEXT.get(wname, ""), "precision": prec, "steps": T,
             "ckpt_every": K, "forward_s": t_fwd, "adjoint_s": t_adj, "adjoint_over_forward": t_adj / t_fwd,
+            "fd_check": fd,
             "Phi": phi, "Phi_forward_check": phi_fwd, "dPhi_dg": list(dG), "max_abs_dPhi_damp": float(abs(dA).max()),
             "what": "gradient of the flux through x = nx/2 averaged over the steps, w.r.t. the per-node wall-potential "
                     "amplitude and the body force"}
+
+
+GOLDEN_C128 = os.path.join(ROOT, "tests", "golden", "channel128_oracle.json")
+
+
+def precision_check(prec):
+    """The error of the storage precision `prec` on the 128x32x32 bottleneck channel after the oracle
+    golden's step count: the summed time-averaged flux against the FP64 oracle's (stored in
+    tests/golden/channel128_oracle.json by an oracle-only script), and max |dn| / max n, max |du^a| / max |u^a|
+    against the GPU FP64 run of the same case (itself the oracle's to round-off)."""
+    from paper_1202_3842_gb300 import studies
+    gold = json.load(open(GOLDEN_C128))
+    precs = ("fp64",) if prec == "fp64" else ("fp64", prec)
+    r = studies.precision(steps=gold["steps"], precs=precs, plane=gold["flux_plane_x"], keep_fields=True)
+    flux = sum(r["fields"][prec]["flux"])
+    fo = sum(gold["flux_time_avg"])
+    return {"workload": "channel128 (128x32x32, slit width 16, sigma 4/6, packing 0.25)", "steps": gold["steps"],
+            "precision": prec, "flux_rel_err_vs_oracle": abs(flux - fo) / abs(fo),
+            "n_rel_err_vs_fp64": r[prec]["n"], "u_rel_err_vs_fp64": r[prec]["u"]}
+
+
+def adjoint_fd_check(wname="channel256adj", T=200, K=20, seed=5):
+    """The FP64 adjoint of the same workload over T steps against central differences of the FP64 forward
+    (h = 1e-4 of the parameter scale): the body force g_x and one random direction over the wall nodes."""
+    import numpy as np
+    from paper_1202_3842_gb300 import inputs
+    w = inputs.WORKLOADS[wname]()
+    arrays = inputs.build_workload(w)
+    M = len(w["sigma"])
+    plane = w["shape"][0] // 2
+
+    def phi(amp, gx):
+        a2 = dict(arrays)
+        a2["amp"] = amp
+        w2 = dict(w)
+        w2["body"] = [(b[0] + gx, b[1], b[2]) for b in w["body"]]
+        sim = make_sim(w2, a2, "fp64")
+        try:
+            sim.set_flux_plane(0, plane)
+            sim.step(T)
+            return sim.flux(-1)[1]
+        finally:
+            sim.close()
+
+    sim = make_sim(w, arrays, "fp64")
+    try:
+        _, dA, dG = sim.adjoint_flux_gradient(T, K, 0, plane)
+    finally:
+        sim.close()
+    rng = np.random.default_rng(seed)
+    d = rng.standard_normal(arrays["amp"].size) * (arrays["phi"] > 0)
+    h = 1e-4 * (1.0 / 3.0)
+    fd_a = (phi(arrays["amp"] + h * d, 0.0) - phi(arrays["amp"] - h * d, 0.0)) / (2 * h)
+    hg = 1e-4 * w["body"][0][0]
+    fd_g = (phi(arrays["amp"], hg) - phi(arrays["amp"], -hg)) / (2 * hg)
+    ad_a = float(dA @ d)
+    return {"steps": T, "ckpt_every": K, "precision": "fp64",
+            "wall_direction": {"adjoint": ad_a, "central_difference": fd_a, "rel_diff": abs(ad_a - fd_a) / abs(fd_a)},
+            "g_x": {"adjoint": float(dG[0]), "central_difference": fd_g,
+                    "rel_diff": abs(float(dG[0]) - fd_g) / abs(fd_g)}}
 
 
 def max_over_ranks(x, dist, device):
@@ -749,6 +811,9 @@ def run_ours(args):
 
     if not args.no_extra and args.prec in ("fp32", "fp64"):
         result["adjoint"] = measure_adjoint(args.prec, T=args.adjoint_steps, K=args.adjoint_ckpt)
+
+    if not args.no_extra and rank == 0:
+        result["precision_error"] = precision_check(args.prec)
 
     if rank == 0 and not args.no_cpu:
         result["cpu_baseline"] = cpu_baseline(w, arrays)

@@ -95,6 +95,8 @@ __global__ void __launch_bounds__(NTA)
         for (int c = 0; c < 3; ++c) X[c] = Cv[a][c] + nF[a][c];
         const T sf0 = (T)-3 * (X[0] * ua[a][0] + X[1] * ua[a][1] + X[2] * ua[a][2]);
         const T om = (T)sp.sp[a].omega_eff, inv = (T)sp.sp[a].inv;
+        const T n0a = (T)sp.sp[a].n0;
+        const T in0 = sp.sp[a].n0 > 0.0 ? (T)(1.0 / sp.sp[a].n0) : (T)0;
         S *fo = dst + pop_off(a, 0, 0, g.N) + i;
         S *go = dst + pop_off(a, 1, 0, g.N) + i;
         [&]<int... P>(std::integer_sequence<int, P...>) {
@@ -108,16 +110,17 @@ __global__ void __launch_bounds__(NTA)
                     const T feq = w * (A + t1);
                     const T Sf = w * (sf0 + (T)3 * cX + (T)9 * cX * cua);
                     const T fs = fv[a][P] + om * (feq - fv[a][P]) + inv * Sf;
-                    Store<S, T>::store(fo + (long long)P * g.N, fs, (T)1);
+                    constexpr T iw = (T)(1.0 / wq(P));
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * n0a, iw * in0);
                     if (sd) {
-                        Store<S, T>::store(go + (long long)P * g.N, fs, (T)1);
+                        Store<S, T>::store(go + (long long)P * g.N, fs, w * n0a, iw * in0);
                     } else {
                         const T cY = cdot<T, P>(nF[a]);
                         const T cC = cdot<T, P>(Cv[a]);
                         const T geq = w * (B + t1);
                         const T Sg = w * (sf0 + (T)3 * cY + (T)18 * cC * cua + (T)9 * cY * cua);
                         const T gs = gv[a][P] + om * (geq - gv[a][P]) + inv * Sg;
-                        Store<S, T>::store(go + (long long)P * g.N, gs, (T)1);
+                        Store<S, T>::store(go + (long long)P * g.N, gs, w * n0a, iw * in0);
                     }
                 }(),
                 ...);

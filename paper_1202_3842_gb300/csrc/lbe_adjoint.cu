@@ -440,8 +440,8 @@ cudaError_t launch_adj_tile(const AdjShellTile &L, cudaStream_t st);
 template <int S, int TZ, int TYB>
 cudaError_t launch_adj_tile2(const AdjShellTile &L, cudaStream_t st);
 
-// FP32: interleaved (Lambda, g Lambda) tiles of the forward kernel (boxes of shell_box); FP64: two planes
-// (boxes of adj_shell_box).
+// FP32: interleaved (Lambda, g Lambda) tiles of 32 x 16 (32 x 8 at S = 8); FP64: two planes.  The
+// tensor maps take their boxes from adj_shell_box, which must match these tiles.
 cudaError_t launch_adj_shell_tile(bool fp64, int S, const AdjShellTile &L, cudaStream_t st) {
     if (!fp64) {
         switch (S) {

@@ -1680,7 +1680,7 @@ lbe_status lbe_adjoint_flux_gradient(lbe_ctx *c, int T, int K, int axis, int pla
                 ATRY(make_map(c, &mapgL[3 * q + cc], (char *)gLpad.p + rb * cc * P, bx, by));
             }
         } else {
-            shell_box(false, c->pairs[q].S, &bx, &by);
+            adj_shell_box(false, c->pairs[q].S, &bx, &by);
             for (int cc = 0; cc < 3; ++cc)
                 ATRY(make_map(c, &mapL[3 * q + cc], (char *)Lpad.p + 2 * rb * cc * P, bx, by, true));
         }

@@ -48,19 +48,41 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     const double n0d = a == 0 ? sp.sp[0].n0 : sp.sp[1].n0;
     const double omd = a == 0 ? sp.sp[0].omega_eff : sp.sp[1].omega_eff;
     const double invd = a == 0 ? sp.sp[0].inv : sp.sp[1].inv;
+    // a warp none of whose nodes has a blocked link pulls without the bounce-back selects
+    const bool plain = !SOLID || __all_sync(0xffffffffu, (m >> 1) == 0u);
     // moments of this thread's species (zero on solid nodes and past the end)
+    constexpr bool DEV = Store<S, T>::shifted;
     T f[Q], gq[Q];
-    T n = 0, Pi = 0, J[3] = {0, 0, 0}, Cv[3] = {0, 0, 0}, nF[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
+    T n = 0, dn = 0, Pi = 0, J[3] = {0, 0, 0}, Cv[3] = {0, 0, 0}, nF[3] = {0, 0, 0}, ua[3] = {0, 0, 0};
     NbrOff o{};
     if (fluid) {
         o = nbr_offsets(g, x, y, z);
         const T n0 = (T)n0d;
         const S *fb = src + pop_off(a, 0, 0, g.N);
         const S *gb = src + pop_off(a, 1, 0, g.N);
-        [&]<int... P>(std::integer_sequence<int, P...>) {
-            ((f[P] = pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
-            ((gq[P] = pull<S, T, P, SOLID>(gb, g.N, i, o, m, n0)), ...);
-        }(std::make_integer_sequence<int, Q>{});
+        // DEV: the populations as deviations from w_p n0 (f, gq below hold f - w_p n0, g - w_p n0)
+        if (plain) {
+            [&]<int... P>(std::integer_sequence<int, P...>) {
+                if constexpr (DEV) {
+                    ((f[P] = pull_dev<S, T, P, false>(fb, g.N, i, o, m, n0)), ...);
+                    ((gq[P] = pull_dev<S, T, P, false>(gb, g.N, i, o, m, n0)), ...);
+                } else {
+                    ((f[P] = pull<S, T, P, false>(fb, g.N, i, o, m, n0)), ...);
+                    ((gq[P] = pull<S, T, P, false>(gb, g.N, i, o, m, n0)), ...);
+                }
+            }(std::make_integer_sequence<int, Q>{});
+        } else {
+            [&]<int... P>(std::integer_sequence<int, P...>) {
+                if constexpr (DEV) {
+                    ((f[P] = pull_dev<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+                    ((gq[P] = pull_dev<S, T, P, SOLID>(gb, g.N, i, o, m, n0)), ...);
+                } else {
+                    ((f[P] = pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+                    ((gq[P] = pull<S, T, P, SOLID>(gb, g.N, i, o, m, n0)), ...);
+                }
+            }(std::make_integer_sequence<int, Q>{});
+        }
+        // n and Pi~ (DEV: their deviations from n0; the rest values sum to n0, and to zero in J~)
         T Pit = 0, Jt[3] = {0, 0, 0};
         [&]<int... P>(std::integer_sequence<int, P...>) {
             ((n += f[P]), ...);
@@ -69,6 +91,10 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
             ((Jt[1] += (T)cy(P) * gq[P]), ...);
             ((Jt[2] += (T)cz(P) * gq[P]), ...);
         }(std::make_integer_sequence<int, Q>{});
+        if constexpr (DEV) {
+            dn = n;
+            n = n0 + dn;
+        }
         const T inv_n = n > (T)0 ? (T)1 / n : (T)0;
         T Cu = 0;
 #pragma unroll
@@ -79,7 +105,7 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
             ua[c] = J[c] * inv_n;
             Cu += Cv[c] * ua[c];
         }
-        Pi = sp.consistent ? Pit + (T)1.5 * Cu : Pit - (T)0.5 * Cu;
+        Pi = sp.consistent ? Pit + (T)1.5 * Cu : Pit - (T)0.5 * Cu;  // DEV: Pi - n0
     }
     // the partner species of the same node, through shared memory; every thread takes part
     T np = 0, Jp[3] = {0, 0, 0};
@@ -107,7 +133,9 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     const T uau = ua[0] * u[0] + ua[1] * u[1] + ua[2] * u[2];
     const T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     const T iso = (T)1.5 * n * ((T)2 * uau - uu);
-    const T A = n - iso;
+    // A and B enter f_eq and g_eq as w_p A, w_p B; DEV: their deviations from n0, so that f_eq and g_eq
+    // come out as deviations from w_p n0 like the populations
+    const T A = (DEV ? dn : n) - iso;
     const T B = Pi - iso;
     T X[3];
 #pragma unroll
@@ -116,6 +144,7 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     const T om = (T)omd;
     const T inv = (T)invd;
     const T in0 = n0d > 0.0 ? (T)(1.0 / n0d) : (T)0;
+    const T n0s = (T)n0d;
     S *fo = dst + pop_off(a, 0, 0, g.N) + i;
     S *go = dst + pop_off(a, 1, 0, g.N) + i;
     [&]<int... P>(std::integer_sequence<int, P...>) {
@@ -135,8 +164,13 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
                 const T fs = f[P] + om * (feq - f[P]) + inv * Sf;
                 const T gs = gq[P] + om * (geq - gq[P]) + inv * Sg;
                 constexpr T iw = (T)(1.0 / wq(P));
-                Store<S, T>::store(fo + (long long)P * g.N, fs, iw * in0);
-                Store<S, T>::store(go + (long long)P * g.N, gs, iw * in0);
+                if constexpr (DEV) {
+                    Store<S, T>::store_dev(fo + (long long)P * g.N, fs, w * n0s, iw * in0);
+                    Store<S, T>::store_dev(go + (long long)P * g.N, gs, w * n0s, iw * in0);
+                } else {
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * n0s, iw * in0);
+                    Store<S, T>::store(go + (long long)P * g.N, gs, w * n0s, iw * in0);
+                }
             }(),
             ...);
     }(std::make_integer_sequence<int, Q>{});
@@ -152,18 +186,35 @@ __global__ void __launch_bounds__(NTP)
     const int a = M == 2 ? (int)(threadIdx.x >> 7) : 0;
     const long long i = M == 2 ? (long long)blockIdx.x * (NTP / 2) + (threadIdx.x & 127)
                                : (long long)blockIdx.x * NTP + threadIdx.x;
-    if (i >= g.N) return;
+    const bool valid = i < g.N;
+    const uint32_t m = valid ? (SOLID ? mask[i] : 0u) : 1u;
+    // a warp none of whose nodes has a blocked link pulls without the bounce-back selects
+    const bool plain = !SOLID || __all_sync(0xffffffffu, (m >> 1) == 0u);
+    if (!valid) return;
     int x, y, z;
     node_xyz(g, i, x, y, z);
-    const uint32_t m = SOLID ? mask[i] : 0u;
     T n = (T)0;
     if (!(m & 1u)) {
         const NbrOff o = nbr_offsets(g, x, y, z);
         const S *fb = pop + pop_off(a, 0, 0, g.N);
         const T n0 = (T)(a == 0 ? n00 : n01);
-        [&]<int... P>(std::integer_sequence<int, P...>) {
-            ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
-        }(std::make_integer_sequence<int, Q>{});
+        // shifted storage: n = n0 + the sum of the deviations
+        if (plain) {
+            [&]<int... P>(std::integer_sequence<int, P...>) {
+                if constexpr (Store<S, T>::shifted)
+                    ((n += pull_dev<S, T, P, false>(fb, g.N, i, o, m, n0)), ...);
+                else
+                    ((n += pull<S, T, P, false>(fb, g.N, i, o, m, n0)), ...);
+            }(std::make_integer_sequence<int, Q>{});
+        } else {
+            [&]<int... P>(std::integer_sequence<int, P...>) {
+                if constexpr (Store<S, T>::shifted)
+                    ((n += pull_dev<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+                else
+                    ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+            }(std::make_integer_sequence<int, Q>{});
+        }
+        if constexpr (Store<S, T>::shifted) n = n0 + n;
         if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
     }
     write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);

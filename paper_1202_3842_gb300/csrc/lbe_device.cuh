@@ -42,11 +42,17 @@ enum : int {
 };
 
 // ---------------------------------------------------------------------------
-// Population storage.  S is the stored type, T the arithmetic type.  The
-// 16-bit forms hold s = f/(w n0) - 1 (populations shifted by their rest value
-// and normalised), so the small deviations keep their relative precision.
-// load() takes wn0 = w_p n0, store() takes its reciprocal 1/(w_p n0) (both
-// unused by the unshifted forms).
+// Population storage.  S is the stored type, T the arithmetic type.  FP64
+// stores the populations f themselves.  The other forms store them shifted by
+// their rest value w_p n0 (n0 the species' mean density over the fluid nodes),
+// so that the stored quantum is relative to the deviation, not to f: FP32
+// stores d = f - w_p n0, the 16-bit forms s = f/(w_p n0) - 1.
+//   load(p, wn0)                 -> f
+//   store(p, f, wn0, iwn0)       <- f
+//   load_dev(p, wn0)             -> d = f - w_p n0
+//   store_dev(p, d, wn0, iwn0)   <- d
+// with wn0 = w_p n0 and iwn0 = 1/(w_p n0).  The fused collision works on the
+// deviations throughout, so its rounding is relative to them as well.
 // ---------------------------------------------------------------------------
 template <typename S, typename T>
 struct Store;
@@ -54,24 +60,32 @@ struct Store;
 template <>
 struct Store<double, double> {
     static __device__ __forceinline__ double load(const double *p, double) { return __ldg(p); }
-    static __device__ __forceinline__ void store(double *p, double v, double) { *p = v; }
+    static __device__ __forceinline__ void store(double *p, double v, double, double) { *p = v; }
+    static __device__ __forceinline__ double load_dev(const double *p, double wn0) { return __ldg(p) - wn0; }
+    static __device__ __forceinline__ void store_dev(double *p, double d, double wn0, double) { *p = d + wn0; }
     static constexpr bool shifted = false;
 };
 template <>
 struct Store<float, float> {
-    static __device__ __forceinline__ float load(const float *p, float) { return __ldg(p); }
-    static __device__ __forceinline__ void store(float *p, float v, float) { *p = v; }
-    static constexpr bool shifted = false;
+    static __device__ __forceinline__ float load(const float *p, float wn0) { return __ldg(p) + wn0; }
+    static __device__ __forceinline__ void store(float *p, float v, float wn0, float) { *p = v - wn0; }
+    static __device__ __forceinline__ float load_dev(const float *p, float) { return __ldg(p); }
+    static __device__ __forceinline__ void store_dev(float *p, float d, float, float) { *p = d; }
+    static constexpr bool shifted = true;
 };
 template <>
 struct Store<__nv_bfloat16, float> {
-    // wn0 = w_p n0 of this population
     static __device__ __forceinline__ float load(const __nv_bfloat16 *p, float wn0) {
         return fmaf(wn0, __bfloat162float(__ldg(p)), wn0);
     }
-    // iwn0 = 1/(w_p n0)
-    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, float iwn0) {
+    static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v, float, float iwn0) {
         *p = __float2bfloat16_rn(fmaf(v, iwn0, -1.0f));
+    }
+    static __device__ __forceinline__ float load_dev(const __nv_bfloat16 *p, float wn0) {
+        return wn0 * __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ void store_dev(__nv_bfloat16 *p, float d, float, float iwn0) {
+        *p = __float2bfloat16_rn(d * iwn0);
     }
     static constexpr bool shifted = true;
 };
@@ -80,8 +94,14 @@ struct Store<__half, float> {
     static __device__ __forceinline__ float load(const __half *p, float wn0) {
         return fmaf(wn0, __half2float(__ldg(p)), wn0);
     }
-    static __device__ __forceinline__ void store(__half *p, float v, float iwn0) {
+    static __device__ __forceinline__ void store(__half *p, float v, float, float iwn0) {
         *p = __float2half_rn(fmaf(v, iwn0, -1.0f));
+    }
+    static __device__ __forceinline__ float load_dev(const __half *p, float wn0) {
+        return wn0 * __half2float(__ldg(p));
+    }
+    static __device__ __forceinline__ void store_dev(__half *p, float d, float, float iwn0) {
+        *p = __float2half_rn(d * iwn0);
     }
     static constexpr bool shifted = true;
 };
@@ -166,13 +186,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Bounded wait for the phase with the given parity to complete: at most `polls` try_wait polls (the
-// kernels use the default, 2^24), then ERR_TMA_WAIT is recorded and the caller gets false.
+// kernels use the default, 2^24) and at most WAIT_NS of wall time, whichever ends first; then
+// ERR_TMA_WAIT is recorded and the caller gets false.  The time bound keeps a launch whose copies do
+// not complete (a box that delivers fewer bytes than its barrier expects, say) from waiting out the
+// polls of every CTA in turn.
 constexpr long long WAIT_POLLS = 1ll << 24;
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err,
                                                   long long polls = WAIT_POLLS) {
-    for (long long it = 0; it < polls; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (long long it = 1; it < polls; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255) == 0 && globaltimer_ns() - t0 > WAIT_NS) break;
     }
     atomicOr(err, ERR_TMA_WAIT);
     return false;

@@ -92,9 +92,29 @@ cudaError_t launch_force_field(Prec p, const Grid &g, const double *V, const dou
 // ---------------------------------------------------------------------------
 // post_p(s) = streamed_p(s + c_p) when s + c_p is a fluid node inside the
 // lattice, else streamed_{opp(p)}(s) (the population bounced back at s).
+// A population given in FP64 (host data, rest state) stored in the storage form: the shifted forms take
+// the deviation f - w_p n0 formed in FP64, so it keeps its precision.
+template <typename S, typename T>
+__device__ __forceinline__ void store_full(S *p, double v, double wn0) {
+    if constexpr (Store<S, T>::shifted)
+        Store<S, T>::store_dev(p, (T)(v - wn0), (T)wn0, wn0 > 0.0 ? (T)(1.0 / wn0) : (T)0);
+    else
+        Store<S, T>::store(p, (T)v, (T)wn0, (T)0);
+}
+
+// The FP64 value of a stored population (the shifted forms add w_p n0 in FP64).
+template <typename S, typename T, int P>
+__device__ __forceinline__ double pull_full(const S *fb, long long N, long long i, const NbrOff &o, uint32_t m,
+                                            double n0) {
+    if constexpr (Store<S, T>::shifted)
+        return (double)pull_dev<S, T, P>(fb, N, i, o, m, (T)n0) + wq(P) * n0;
+    else
+        return (double)pull<S, T, P>(fb, N, i, o, m, (T)n0);
+}
+
 template <typename S, typename T>
 __global__ void k_unstream(Grid g, const uint32_t *__restrict__ mask, const double *__restrict__ f,
-                           const double *__restrict__ gq, S *__restrict__ pop, int a, T n0) {
+                           const double *__restrict__ gq, S *__restrict__ pop, int a, double n0) {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     int x, y, z;
@@ -115,16 +135,15 @@ __global__ void k_unstream(Grid g, const uint32_t *__restrict__ mask, const doub
                 gv = gq[(long long)opp(p) * g.N + s];
             }
         }
-        const T iwn0 = (T)1 / ((T)wq(p) * n0);
-        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)fv, iwn0);
-        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)gv, iwn0);
+        store_full<S, T>(pop + pop_off(a, 0, p, g.N) + s, fv, wq(p) * n0);
+        store_full<S, T>(pop + pop_off(a, 1, p, g.N) + s, gv, wq(p) * n0);
     }
 }
 
 // Rest state: streamed f_p(r) = w_p n(r) and g_p(r) = w_p Pi(r) on fluid nodes (Pi = n without pi).
 template <typename S, typename T>
 __global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const double *__restrict__ n,
-                             const double *__restrict__ pi, S *__restrict__ pop, int a, T n0) {
+                             const double *__restrict__ pi, S *__restrict__ pop, int a, double n0) {
     long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.N) return;
     int x, y, z;
@@ -142,14 +161,13 @@ __global__ void k_rest_state(Grid g, const uint32_t *__restrict__ mask, const do
             v = wq(p) * n[u];
             vg = wq(p) * gsrc[u];
         }
-        const T iwn0 = (T)1 / ((T)wq(p) * n0);
-        Store<S, T>::store(pop + pop_off(a, 0, p, g.N) + s, (T)v, iwn0);
-        Store<S, T>::store(pop + pop_off(a, 1, p, g.N) + s, (T)vg, iwn0);
+        store_full<S, T>(pop + pop_off(a, 0, p, g.N) + s, v, wq(p) * n0);
+        store_full<S, T>(pop + pop_off(a, 1, p, g.N) + s, vg, wq(p) * n0);
     }
 }
 
 template <typename S, typename T>
-__global__ void k_stream_out(Grid g, const uint32_t *__restrict__ mask, const S *__restrict__ pop, int a, T n0,
+__global__ void k_stream_out(Grid g, const uint32_t *__restrict__ mask, const S *__restrict__ pop, int a, double n0,
                              double *__restrict__ f, double *__restrict__ gq) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
@@ -163,8 +181,8 @@ __global__ void k_stream_out(Grid g, const uint32_t *__restrict__ mask, const S 
         constexpr int P = decltype(Pc)::value;
         double fv = 0.0, gv = 0.0;
         if (!(m & 1u)) {
-            fv = (double)pull<S, T, P>(fb, g.N, i, o, m, n0);
-            gv = (double)pull<S, T, P>(gb, g.N, i, o, m, n0);
+            fv = pull_full<S, T, P>(fb, g.N, i, o, m, n0);
+            gv = pull_full<S, T, P>(gb, g.N, i, o, m, n0);
         }
         f[(long long)P * g.N + i] = fv;
         gq[(long long)P * g.N + i] = gv;
@@ -184,21 +202,21 @@ __global__ void k_stream_out(Grid g, const uint32_t *__restrict__ mask, const S 
 cudaError_t launch_unstream(Prec p, const Grid &g, const uint32_t *mask, const double *f, const double *gq,
                             void *pop, int a, double n0, cudaStream_t st) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
-    LBE_DISPATCH_PREC(p, (k_unstream<S, T><<<nb, NT, 0, st>>>(g, mask, f, gq, (S *)pop, a, (T)n0)));
+    LBE_DISPATCH_PREC(p, (k_unstream<S, T><<<nb, NT, 0, st>>>(g, mask, f, gq, (S *)pop, a, n0)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_rest_state(Prec p, const Grid &g, const uint32_t *mask, const double *n, void *pop, int a,
                               double n0, cudaStream_t st, const double *pi) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
-    LBE_DISPATCH_PREC(p, (k_rest_state<S, T><<<nb, NT, 0, st>>>(g, mask, n, pi, (S *)pop, a, (T)n0)));
+    LBE_DISPATCH_PREC(p, (k_rest_state<S, T><<<nb, NT, 0, st>>>(g, mask, n, pi, (S *)pop, a, n0)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const void *pop, int a, double n0,
                               double *f, double *gq, cudaStream_t st) {
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
-    LBE_DISPATCH_PREC(p, (k_stream_out<S, T><<<nb, NT, 0, st>>>(g, mask, (const S *)pop, a, (T)n0, f, gq)));
+    LBE_DISPATCH_PREC(p, (k_stream_out<S, T><<<nb, NT, 0, st>>>(g, mask, (const S *)pop, a, n0, f, gq)));
     return cudaGetLastError();
 }
 
@@ -220,9 +238,14 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
         if (!(m & 1u)) {
             const S *fb = pop + pop_off(a, 0, 0, g.N);
             const T n0 = (T)n0v.v[a];
+            // shifted storage: n = n0 + the sum of the deviations
             [&]<int... P>(std::integer_sequence<int, P...>) {
-                ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+                if constexpr (Store<S, T>::shifted)
+                    ((n += pull_dev<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+                else
+                    ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
             }(std::make_integer_sequence<int, Q>{});
+            if constexpr (Store<S, T>::shifted) n = n0 + n;
             if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
         }
         write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);
@@ -232,7 +255,7 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
 cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_t *mask, bool solid, int M,
                            const double *n0, void *npad, int *err, cudaStream_t st) {
     // one species: one thread per node at 32-42 registers (lbe_collide_pair.cu); measured faster than this
-    // kernel for one species (256^3 well 0.42 -> 0.31 ms) and slower for two (0.30 -> 0.32 ms)
+    // kernel for one species (256^3 well 0.42 -> 0.31 ms) and slower for two (0.29 -> 0.31 ms)
     if (M == 1) return launch_density_pair(p, g, pop, mask, solid, M, n0, npad, err, st);
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
     N0Vec n0v;
@@ -397,8 +420,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (M == 1 ? 3 : 2) : 1)
                     const T fs = fa[P] + om * (feq - fa[P]) + inv * Sf;
                     const T gs = ga[P] + om * (geq - ga[P]) + inv * Sg;
                     constexpr T iw = (T)(1.0 / wq(P));
-                    Store<S, T>::store(fo + (long long)P * g.N, fs, iw * in0);
-                    Store<S, T>::store(go + (long long)P * g.N, gs, iw * in0);
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * (T)sp.sp[a].n0, iw * in0);
+                    Store<S, T>::store(go + (long long)P * g.N, gs, w * (T)sp.sp[a].n0, iw * in0);
                 }(),
                 ...);
         }(std::make_integer_sequence<int, Q>{});

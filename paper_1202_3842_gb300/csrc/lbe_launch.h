@@ -109,7 +109,7 @@ void contact_box(bool fp64, int M, int RB, int *bx, int *by);
 cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStream_t st);
 bool shell_supported(bool fp64, int S);
 void shell_box(bool fp64, int S, int *bx, int *by);      // forward: FP32 boxes count 8-byte (n, g n) elements
-void adj_shell_box(bool fp64, int S, int *bx, int *by);  // shell transpose: boxes of the compute type
+void adj_shell_box(bool fp64, int S, int *bx, int *by);  // shell transpose: boxes of its own tiles
 // K4: fused moments + DD-TR collision + pull streaming.
 cudaError_t launch_collide(Prec p, const Grid &g, const void *src, void *dst, const uint32_t *mask, bool solid,
                            const void *C, const void *F, const StepParams &sp, double *flux_buf,
@@ -182,7 +182,7 @@ struct AdjShell {
 // Shell sums of the transpose of pair (a, b): three launches, one per component.
 struct AdjShellTile {
     const Grid *grid;
-    const CUtensorMap *maps_L;   // [3] padded Lambda_c, box of shell_box(S)
+    const CUtensorMap *maps_L;   // [3] padded Lambda_c, box of adj_shell_box(S)
     const CUtensorMap *maps_gL;  // [3] padded (g Lambda)_c
     const void *npad_b;
     const void *g_ab;

@@ -67,6 +67,19 @@ __device__ __forceinline__ T pull(const S *__restrict__ fg_base, long long N, lo
     }
 }
 
+// The same pull, returning the deviation f - w_p n0 of the pulled population (see Store).
+template <typename S, typename T, int P, bool SOLID = true>
+__device__ __forceinline__ T pull_dev(const S *__restrict__ fg_base, long long N, long long i, const NbrOff &o,
+                                      uint32_t m, T n0) {
+    const T wn0 = (T)wq(P) * n0;
+    if constexpr (SOLID) {
+        const long long off = (m & (1u << P)) ? (long long)opp(P) * N + i : (long long)P * N + i + src_off<P>(o);
+        return Store<S, T>::load_dev(fg_base + off, wn0);
+    } else {
+        return Store<S, T>::load_dev(fg_base + (long long)P * N + i + src_off<P>(o), wn0);
+    }
+}
+
 template <typename T, int P>
 __device__ __forceinline__ T cdot(const T *v) {
     T r = (T)0;

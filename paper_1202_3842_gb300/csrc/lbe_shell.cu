@@ -23,9 +23,9 @@ cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStrea
             case 1: return launch_zb<1, 3, 16>(L, st);
             case 2: return launch_zb<2, 3, 16>(L, st);
             case 3: return launch_zb<3, 3, 16>(L, st);
-            case 4: return launch_zb<4, 3, 16>(L, st);
-            case 5: return launch_zb<5, 3, 16>(L, st);
-            case 6: return launch_zb<6, 3, 16>(L, st);
+            case 4: return launch_zb<4, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
+            case 5: return launch_zb<5, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
+            case 6: return launch_zb<6, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
             case 7: return launch_zb<7, 2, 16>(L, st);
             case 8: return launch_zb<8, 1, 8>(L, st);
             default: return cudaErrorInvalidValue;
@@ -45,10 +45,13 @@ cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStrea
 
 bool shell_supported(bool fp64, int S) { return S >= 1 && S <= (fp64 ? 7 : 8); }
 
-// Box of the shell-transpose tiles (separate planes of the compute type; lbe_adj_shell.cuh).
+// Box of the shell-transpose tiles (lbe_adj_shell.cuh, dispatched in lbe_adjoint.cu).  FP32: the
+// interleaved 8-byte (Lambda, g Lambda) elements of a 32 x 16 tile (32 x 8 at S = 8), the tile the
+// transpose itself runs, which stays at 16 rows whatever the forward kernel's rows are; FP64: the
+// forward kernel's box of two separate planes.
 void adj_shell_box(bool fp64, int S, int *bx, int *by) {
     if (!fp64) {
-        *bx = ((32 + 2 * S + 3) + 3) / 4 * 4;
+        *bx = ((32 + 2 * S + 1) + 1) / 2 * 2;
         *by = (S <= 7 ? 16 : 8) + 2 * S;
         return;
     }
@@ -58,7 +61,7 @@ void adj_shell_box(bool fp64, int S, int *bx, int *by) {
 void shell_box(bool fp64, int S, int *bx, int *by) {
     if (!fp64) {  // interleaved 8-byte elements; 32 x 16 outputs per plane (32 x 8 at S = 8)
         *bx = ((32 + 2 * S + 1) + 1) / 2 * 2;
-        *by = (S <= 7 ? 16 : 8) + 2 * S;
+        *by = (S >= 4 && S <= 6 ? LBE_SHELL_TY : (S <= 7 ? 16 : 8)) + 2 * S;
         return;
     }
 #define LBE_BOX(s)                              \

@@ -3,6 +3,16 @@
 
 #include <utility>
 
+// Tile of the FP32 shell kernel for pair diameters 4 to 6 (the common ones): TZ outputs per thread
+// along z and TY thread rows (defaults 6 and 12, the fastest of a measured sweep; a build may set
+// others to measure them).
+#ifndef LBE_SHELL_TZ
+#define LBE_SHELL_TZ 6
+#endif
+#ifndef LBE_SHELL_TY
+#define LBE_SHELL_TY 12
+#endif
+
 namespace lbe {
 
 // Contact shell of integer diameter S (Appendix, hard-sphere C^{alpha,mf}: the
@@ -151,7 +161,7 @@ struct ShellTileZ2 {
     static constexpr int PLANE_BYTES = ((PLANE * 8) + 127) / 128 * 128;
     static constexpr int SLOT_BYTES = PLANE_BYTES;
     static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
-    static constexpr int LZ = TZ == 3 ? 18 : 16;  // planes per CTA, a multiple of TZ
+    static constexpr int LZ = (16 + TZ - 1) / TZ * TZ;  // planes per CTA, a multiple of TZ
 };
 
 }  // namespace lbe

@@ -5,5 +5,5 @@ namespace lbe {
 template cudaError_t launch_zb<1, 3, 16>(const ShellLaunch &, cudaStream_t);
 template cudaError_t launch_zb<2, 3, 16>(const ShellLaunch &, cudaStream_t);
 template cudaError_t launch_zb<3, 3, 16>(const ShellLaunch &, cudaStream_t);
-template cudaError_t launch_zb<4, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<4, LBE_SHELL_TZ, LBE_SHELL_TY>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

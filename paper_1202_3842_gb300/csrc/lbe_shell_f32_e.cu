@@ -2,5 +2,5 @@
 #include "lbe_shell_kernels.cuh"
 
 namespace lbe {
-template cudaError_t launch_zb<6, 3, 16>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_zb<6, LBE_SHELL_TZ, LBE_SHELL_TY>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

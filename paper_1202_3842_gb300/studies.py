@@ -16,6 +16,8 @@ numbers; ``python -m paper_1202_3842_gb300.studies <study> [--quick]`` prints on
 - ``init``: the transient of the spurious current from the rest state and from the quasi-pressure
   state of the second distribution.
 - ``visc``: stability with and without the viscous Enskog force.
+- ``well_map``: stability of the method over packing and well depth at the production well's diameter
+  and relaxation time (sigma 6, tau 0.8) on a 64^3 lattice.
 - ``precision``: the storage precisions (FP32 and the shifted BF16 and FP16 forms) against FP64 on the
   128x32x32 bottleneck channel: density, velocity and time-averaged flux after the same steps.
 
@@ -277,6 +279,44 @@ def visc(cases=("well48", "channel128", "well24"), steps=600, prec="fp32", check
     return out
 
 
+def well_map(etas=(0.1, 0.15, 0.2, 0.25, 0.3), depths=(0.5, 1.0, 2.0), L=64, radius=6.0, sigma=6.0, tau=0.8,
+             steps=2000, check=50, prec="fp32"):
+    """Stability of the DD-TR scheme (printed moment recovery) in the one-component Gaussian well at the
+    diameter and relaxation time of the production-size well (sigma 6, tau 0.8), over packing and well
+    depth, on a periodic L^3 lattice with the well radius scaled to the lattice (256^3 with radius 24
+    becomes 64^3 with radius 6).  For each (packing, depth): the step by which a negative or non-finite
+    density appeared (checked every `check` steps), or, for a run that lasts `steps`, max|u|/v_T and the
+    density residual max|n(t) - n(t - check)| / (check n0) at the end."""
+    out = {}
+    for eta in etas:
+        for depth in depths:
+            w = inputs.well_workload((L, L, L), sigma, eta, tau, depth, radius)
+            arr = inputs.build_workload(w)
+            sim = lbe.Simulation(w["shape"], w["periodic"], 1, prec, check_every=check)
+            res = {}
+            try:
+                sim.set_species(0, sigma, tau)
+                sim.set_potential(0, arr["V"][0])
+                sim.init_density(0, arr["n"][0])
+                done = 0
+                try:
+                    while done < steps - check:
+                        sim.step(check)
+                        done += check
+                    sim.residual()
+                    sim.step(check)
+                    done += check
+                    r = sim.residual()
+                    u = sim.velocity(-1)
+                    res = {"stable_steps": done, "u": float(np.sqrt((u ** 2).sum(0)).max() / CS), "residual": r}
+                except lbe.LbeError:
+                    res = {"diverged_by_step": done + check}
+            finally:
+                sim.close()
+            out["%g/%g" % (eta, depth)] = res
+    return {"sigma": sigma, "tau": tau, "L": L, "radius": radius, "steps": steps, "runs": out}
+
+
 def precision(steps=1000, precs=("fp64", "fp32", "bf16", "fp16"), workload="channel128", plane=None,
               keep_fields=False):
     """Each storage precision against the FP64 run of the same workload and step count (the FP64 path
@@ -336,9 +376,10 @@ QUICK = {
     "init": dict(xis=(6,), steps=500),
     "visc": dict(cases=("well48", "well24"), steps=200),
     "precision": dict(steps=200),
+    "well_map": dict(etas=(0.1, 0.3), depths=(0.5, 2.0), L=32, radius=3.0, steps=300),
 }
 STUDIES = dict(spurious=spurious, mixture=mixture, stability=stability, ideal_gas=ideal_gas,
-               divergence=divergence, init=init, visc=visc, precision=precision)
+               divergence=divergence, init=init, visc=visc, precision=precision, well_map=well_map)
 
 
 def main(argv=None):

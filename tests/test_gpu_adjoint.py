@@ -199,7 +199,7 @@ def full_size_adjoint():
 
 
 def test_full_size_fp64_adjoint_matches_central_differences(full_size_adjoint):
-    """The benchmark spec: the adjoint within 1e-4 relative of central differences (h = 1e-4 of the parameter
+    """The adjoint within 1e-4 relative of central differences (h = 1e-4 of the parameter
     scale), here on the full-size adjoint channel: four random directions over the wall nodes, four
     single wall nodes and the body force g_x, each against two FP64 forward runs of the GPU."""
     S = full_size_adjoint
@@ -228,11 +228,12 @@ def test_full_size_fp64_adjoint_matches_central_differences(full_size_adjoint):
 
 def test_full_size_fp32_adjoint_against_fp64(full_size_adjoint):
     """The FP32 adjoint on the same full-size case, against the FP64 adjoint (FP32 forward and adjoint
-    arithmetic over 200 steps): Phi within the benchmark spec's FP32 flux bound of 1e-3, the wall-amplitude
-    gradient within 1e-2 of its largest entry, dPhi/dg_x within 1e-3."""
+    arithmetic over 200 steps).  Measured: Phi 1.6e-4 relative, the wall-amplitude gradient 7.7e-6 of its
+    largest entry, dPhi/dg_x 2.7e-6 relative.  Held to the FP32 flux bound of 1e-3 on Phi and to
+    about twice the measured errors on the gradients (2e-5 and 1e-5)."""
     Phi64, dA64, dG64 = full_size_adjoint["fp64"]
     Phi32, dA32, dG32 = full_size_adjoint["fp32"]
     err = {"Phi": abs(Phi32 - Phi64) / abs(Phi64), "dA": float(np.abs(dA32 - dA64).max() / np.abs(dA64).max()),
            "dG": abs(dG32[0] - dG64[0]) / abs(dG64[0])}
     print("full-size FP32 adjoint errors against FP64:", err)
-    assert err["Phi"] <= 1e-3 and err["dA"] <= 1e-2 and err["dG"] <= 1e-3, err
+    assert err["Phi"] <= 1e-3 and err["dA"] <= 2e-5 and err["dG"] <= 1e-5, err
