@@ -206,6 +206,8 @@ KERNEL_SOURCES = {
     "contact": ["paper_1202_3842_gb300/csrc/lbe_contact.cu", "paper_1202_3842_gb300/csrc/lbe_contact.cuh",
                 "paper_1202_3842_gb300/csrc/lbe_device.cuh"],
     "flux": ["paper_1202_3842_gb300/csrc/lbe_kernels.cu"],
+    "shell_spectral": ["paper_1202_3842_gb300/csrc/lbe_spectral.cu"],
+    "contact_spectral": ["paper_1202_3842_gb300/csrc/lbe_spectral.cu"],
 }
 
 
@@ -424,6 +426,8 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
     HBM.  K3 is the roofline of the dominant-kernel entry when it dominates."""
     rb = 8 if prec == "fp64" else 4
     out = {}
+    name = w.get("name", "")
+    hbm_src = "measured hbm_gbs (STREAM-style copy, MEASURED_PEAKS.json)"
 
     def t_of(k):
         return stages[k][0] / stages[k][1] * 1e-3 if k in stages and stages[k][1] else None
@@ -433,12 +437,13 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
         b = N * M * (QPOP * sb + rb)
         out["density"] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
                           "achieved_gbs": b / t / 1e9, "peak_gbs": hbm, "frac": b / t / 1e9 / hbm,
-                          "frac_of_measured_hbm": b / t / 1e9 / hbm}
+                          "frac_of_measured_hbm": b / t / 1e9 / hbm, "peak_source": hbm_src,
+                          "traffic": traffic_for("density", name, prec)}
     t = t_of("collide")
     if t:
         b = N * M * 4 * QPOP * sb
         e = {"algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3, "achieved_gbs": b / t / 1e9,
-             "frac_of_measured_hbm": b / t / 1e9 / hbm}
+             "frac_of_measured_hbm": b / t / 1e9 / hbm, "traffic": traffic_for("collide", name, prec)}
         if prec == "fp64":
             fl = N * M * K4_FLOPS_PER_NODE_SPECIES
             e.update({"bound": "alu", "algorithmic_flops_per_launch": fl, "achieved_tflops": fl / t / 1e12,
@@ -447,7 +452,7 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
                                      "species counted from the source: %d" % (FP64_NOMINAL_TFLOPS,
                                                                               K4_FLOPS_PER_NODE_SPECIES)})
         else:
-            e.update({"bound": "hbm", "peak_gbs": hbm, "frac": b / t / 1e9 / hbm})
+            e.update({"bound": "hbm", "peak_gbs": hbm, "frac": b / t / 1e9 / hbm, "peak_source": hbm_src})
         out["collide"] = e
     t = t_of("contact")
     if t:
@@ -458,7 +463,8 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
             out["contact"] = {"bound": "smem", "algorithmic_smem_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
                               "achieved_gbs": b / t / 1e9, "peak_gbs": peak, "frac": b / t / 1e9 / peak,
                               "peak_source": "shared-memory loads: %d SMs x 128 B/clock x %.0f MHz" % (sms, clk),
-                              "note": "ball sums from a TMA-staged ring: %d shared loads per node" % loads}
+                              "note": "ball sums from a TMA-staged ring: %d shared loads per node" % loads,
+                              "traffic": traffic_for("contact", name, prec)}
         else:
             # spectral contact stage: M densities embedded and transformed forward, ball spectra applied,
             # M inverse transforms, then the pointwise contact kernel (ball averages in, g and g n out)
@@ -471,9 +477,11 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
                  + M * rb * Lr + M * M * rb * (N + Lr))     # contact: averages in; g_ab, g_ab n_b out
             out["contact"] = {"bound": "hbm", "algorithmic_bytes_per_launch": b, "avg_launch_ms": t * 1e3,
                               "achieved_gbs": b / t / 1e9, "peak_gbs": hbm, "frac": b / t / 1e9 / hbm,
-                              "frac_of_measured_hbm": b / t / 1e9 / hbm, "fft_grid": L}
-    if "shell" in stages and roof.get("bound") == "alu":
-        out["shell"] = {"bound": "alu", "achieved_tflops": roof["achieved"], "frac": roof["frac"]}
+                              "frac_of_measured_hbm": b / t / 1e9 / hbm, "fft_grid": L, "peak_source": hbm_src,
+                              "traffic": traffic_for("contact_spectral", name, prec)}
+    if "shell" in stages and roof.get("kernel", "").startswith("k_shell_force"):
+        out["shell"] = {"bound": roof["bound"], "achieved_tflops": roof["achieved"], "peak_tflops": roof["peak"],
+                        "frac": roof["frac"], "peak_source": roof.get("peak_source"), "traffic": roof.get("traffic")}
     return out
 
 
@@ -564,7 +572,8 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
         Lc = (L[0] // 2 + 1) * L[1] * L[2]
         nf, ni, nS = M * M, 3 * M * M + 3 * M, len(set(S for S in [
             int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]))
-        common = {"kernel": "K3 spectral (cuFFT transforms + k_spec_embed/multiply/combine)", "traffic": None,
+        common = {"kernel": "K3 spectral (cuFFT transforms + k_spec_embed/multiply/combine)",
+                  "traffic": traffic_for("shell_spectral", wname, prec),
                   "fft_grid": L, "launches": dom_n, "avg_launch_ms": per_launch_ms}
         if prec == "fp64":
             flops = (nf + ni) * 2.5 * Lr * math.log2(Lr)
