@@ -1,9 +1,10 @@
 // Dispatch of the shell-force kernels by precision and pair diameter, and the
-// host-side shell helpers.  FP32 uses the z-blocked kernel on the interleaved
-// field (n_b, g_ab n_b): 32 x 16 threads with three outputs per thread along z
-// up to diameter 6 and two at 7, 32 x 8 threads with one output at 8.  The
-// FP64 path uses the plain kernel (one output per thread and plane).  The kernels are instantiated in lbe_shell_f32_*.cu
-// and lbe_shell_f64.cu.
+// host-side shell helpers.  FP32 reads the interleaved field (n_b, g_ab n_b):
+// diameters 4 to 6 run the y-blocked kernel (32 x 8 threads, two rows and
+// three planes of outputs per thread); 1 to 3 the z-blocked one with three
+// outputs along z on 32 x 16 threads, 7 with two, 8 with one on 32 x 8.  The
+// FP64 path uses the plain kernel (one output per thread and plane).  The
+// kernels are instantiated in lbe_shell_f32_*.cu and lbe_shell_f64.cu.
 #include "lbe_device.cuh"
 #include "lbe_launch.h"
 #include "lbe_shell.cuh"
@@ -14,6 +15,14 @@ template <typename T, int S>
 cudaError_t launch_one(const ShellLaunch &L, cudaStream_t st);
 template <int S, int TZ, int TYB>
 cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st);
+template <int S, int TZ, int TYT>
+cudaError_t launch_yb(const ShellLaunch &L, cudaStream_t st);
+
+#if LBE_SHELL_YB
+#define LBE_MID(S) launch_yb<S, LBE_SHELL_YTZ, LBE_SHELL_YTY>(L, st)
+#else
+#define LBE_MID(S) launch_zb<S, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st)
+#endif
 
 
 
@@ -23,9 +32,9 @@ cudaError_t launch_shell_force(bool fp64, int S, const ShellLaunch &L, cudaStrea
             case 1: return launch_zb<1, 3, 16>(L, st);
             case 2: return launch_zb<2, 3, 16>(L, st);
             case 3: return launch_zb<3, 3, 16>(L, st);
-            case 4: return launch_zb<4, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
-            case 5: return launch_zb<5, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
-            case 6: return launch_zb<6, LBE_SHELL_TZ, LBE_SHELL_TY>(L, st);
+            case 4: return LBE_MID(4);
+            case 5: return LBE_MID(5);
+            case 6: return LBE_MID(6);
             case 7: return launch_zb<7, 2, 16>(L, st);
             case 8: return launch_zb<8, 1, 8>(L, st);
             default: return cudaErrorInvalidValue;
@@ -61,7 +70,7 @@ void adj_shell_box(bool fp64, int S, int *bx, int *by) {
 void shell_box(bool fp64, int S, int *bx, int *by) {
     if (!fp64) {  // interleaved 8-byte elements; 32 x 16 outputs per plane (32 x 8 at S = 8)
         *bx = ((32 + 2 * S + 1) + 1) / 2 * 2;
-        *by = (S >= 4 && S <= 6 ? LBE_SHELL_TY : (S <= 7 ? 16 : 8)) + 2 * S;
+        *by = (S >= 4 && S <= 6 ? (LBE_SHELL_YB ? 2 * LBE_SHELL_YTY : LBE_SHELL_TY) : (S <= 7 ? 16 : 8)) + 2 * S;
         return;
     }
 #define LBE_BOX(s)                              \

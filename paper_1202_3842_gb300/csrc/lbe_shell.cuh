@@ -3,14 +3,25 @@
 
 #include <utility>
 
-// Tile of the FP32 shell kernel for pair diameters 4 to 6 (the common ones): TZ outputs per thread
-// along z and TY thread rows (defaults 6 and 12, the fastest of a measured sweep; a build may set
-// others to measure them).
+// FP32 shell tiles for pair diameters 4 to 6 (the common ones); the defaults are the fastest of measured
+// sweeps, and a build may set others to measure them.  Z-blocked kernel: LBE_SHELL_TZ outputs per thread
+// along z on LBE_SHELL_TY thread rows.
 #ifndef LBE_SHELL_TZ
 #define LBE_SHELL_TZ 6
 #endif
 #ifndef LBE_SHELL_TY
 #define LBE_SHELL_TY 12
+#endif
+// Y-blocked kernel, the one these diameters run when LBE_SHELL_YB is 1: two output rows per thread,
+// LBE_SHELL_YTZ outputs along z, LBE_SHELL_YTY thread rows.
+#ifndef LBE_SHELL_YB
+#define LBE_SHELL_YB 1
+#endif
+#ifndef LBE_SHELL_YTZ
+#define LBE_SHELL_YTZ 3
+#endif
+#ifndef LBE_SHELL_YTY
+#define LBE_SHELL_YTY 8
 #endif
 
 namespace lbe {
@@ -163,5 +174,42 @@ struct ShellTileZ2 {
     static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
     static constexpr int LZ = (16 + TZ - 1) / TZ * TZ;  // planes per CTA, a multiple of TZ
 };
+
+// Tile of the FP32 y-blocked forward kernel (k_shell_force_yb): 32 x TYT threads, each with two output
+// rows (y, y + 1) and TZ outputs along z, so a plane of the tile holds 32 x 2TYT outputs.  The ring holds
+// the 2S + TZ planes in use plus up to TZ in flight, as many of those as fit in 227 KB of shared memory.
+template <int S, int TZ, int TYT_ = 8>
+struct ShellTileY {
+    static constexpr int A = 2;
+    static constexpr int TX = 32;
+    static constexpr int TYT = TYT_;     // thread rows
+    static constexpr int TY = 2 * TYT;   // output rows
+    static constexpr int BX = ((TX + 2 * S + A - 1) + A - 1) / A * A;
+    static constexpr int BY = TY + 2 * S;
+    static constexpr int PLANE = BX * BY;
+    static constexpr int PLANE_BYTES = ((PLANE * 8) + 127) / 128 * 128;
+    static constexpr int SLOT_BYTES = PLANE_BYTES;
+    static constexpr int NK = 2 * S + TZ;
+    static constexpr int RFIT = (227 * 1024 - 256 - 128) / SLOT_BYTES;
+    static constexpr int R = RFIT < NK + TZ ? RFIT : NK + TZ;
+    static_assert(R >= NK, "the planes one step reads do not fit in shared memory");
+    static constexpr int SMEM = R * SLOT_BYTES + 256 + 128;
+    static constexpr int LZ = (16 + TZ - 1) / TZ * TZ;
+};
+
+// Column bits of the shell: bit (ez + S) of col_mask(S, ex, ey) is set when (ex, ey, ez) is in the shell.
+__host__ __device__ constexpr unsigned col_mask(int S, int ex, int ey) {
+    unsigned m = 0;
+    for (int z = -S; z <= S; ++z)
+        if (in_shell(S, ex, ey, z)) m |= 1u << (z + S);
+    return m;
+}
+// Largest |ey| with a nonempty column at ex (-1 if none).
+__host__ __device__ constexpr int col_eymax(int S, int ex) {
+    int r = -1;
+    for (int y = 0; y <= S; ++y)
+        if (col_mask(S, ex, y)) r = y;
+    return r;
+}
 
 }  // namespace lbe

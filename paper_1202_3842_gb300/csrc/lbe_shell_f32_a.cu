@@ -6,4 +6,5 @@ template cudaError_t launch_zb<1, 3, 16>(const ShellLaunch &, cudaStream_t);
 template cudaError_t launch_zb<2, 3, 16>(const ShellLaunch &, cudaStream_t);
 template cudaError_t launch_zb<3, 3, 16>(const ShellLaunch &, cudaStream_t);
 template cudaError_t launch_zb<4, LBE_SHELL_TZ, LBE_SHELL_TY>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_yb<4, LBE_SHELL_YTZ, LBE_SHELL_YTY>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

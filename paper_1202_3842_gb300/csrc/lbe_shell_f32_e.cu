@@ -3,4 +3,5 @@
 
 namespace lbe {
 template cudaError_t launch_zb<6, LBE_SHELL_TZ, LBE_SHELL_TY>(const ShellLaunch &, cudaStream_t);
+template cudaError_t launch_yb<6, LBE_SHELL_YTZ, LBE_SHELL_YTY>(const ShellLaunch &, cudaStream_t);
 }  // namespace lbe

@@ -356,6 +356,245 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// y-blocked variant (FP32, pair diameters 4 to 6): each thread produces two output rows (y, y + 1)
+// and TZ outputs along z.  The half shell is walked column by column with ex fixed and ey ascending.
+// Output row y takes the "+" row y + ey and the "-" row y - ey of column (ex, ey); output row y + 1
+// takes y + 1 + ey and y + 1 - ey.  The "+" row y + 1 + ey is also the next column's "+" row of output y,
+// and the "-" row y - ey the next column's "-" row of output y + 1, so each column step loads one new
+// "+" row and one new "-" row (the planes both columns need) and keeps the other two in registers:
+// about half the shared loads per output of the one-row walk, with the same +-e pairing.
+// ---------------------------------------------------------------------------
+template <int S, int TZ>
+__host__ __device__ constexpr bool y_plus_needs(unsigned m, int k) {  // plane k = t + ez + S read by some t
+    for (int t = 0; t < TZ; ++t) {
+        int ez = k - t - S;
+        if (ez >= -S && ez <= S && ((m >> (ez + S)) & 1u)) return true;
+    }
+    return false;
+}
+template <int S, int TZ>
+__host__ __device__ constexpr bool y_minus_needs(unsigned m, int k) {  // plane k = t - ez + S
+    for (int t = 0; t < TZ; ++t) {
+        int ez = t + S - k;
+        if (ez >= -S && ez <= S && ((m >> (ez + S)) & 1u)) return true;
+    }
+    return false;
+}
+
+template <int S, int TZ, int TYT, int EX, int EY>
+__device__ __forceinline__ void y_column(const f2 *const *sb, f2 *Pc, f2 *Mc, f2 (*acc)[TZ][3]) {
+    using Tl = ShellTileY<S, TZ, TYT>;
+    constexpr int NK = 2 * S + TZ;
+    constexpr unsigned m = col_mask(S, EX, EY);
+    constexpr int hi = col_eymax(S, EX);
+    constexpr unsigned mn = EY < hi ? col_mask(S, EX, EY + 1) : 0u;
+    constexpr int offP = (EY + 1) * Tl::BX + EX;  // "+" row EY + 1 (x + ex)
+    constexpr int offM = -EY * Tl::BX - EX;       // "-" row -EY (x - ex)
+    f2 Pn[NK], Mn[NK];
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+        (
+            [&] {
+                if constexpr (y_plus_needs<S, TZ>(m | mn, K)) Pn[K] = sb[K][offP];
+                if constexpr (y_minus_needs<S, TZ>(m | mn, K)) Mn[K] = sb[K][offM];
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, NK>{});
+    // row y: "+" row EY carried in Pc, "-" row -EY loaded now; row y + 1: "+" row EY + 1 loaded now, "-" row
+    // 1 - EY carried in Mc
+    [&]<int... J>(std::integer_sequence<int, J...>) {
+        (
+            [&] {
+                // points in order of ez, the TZ outputs of one point side by side
+                constexpr int t = J % TZ;
+                constexpr int ez = J / TZ - S;
+                if constexpr ((m >> (ez + S)) & 1u) {
+                    constexpr double len = ct_sqrt((double)(EX * EX + EY * EY + ez * ez));
+                    const f2 d0 = f2sub(Pc[t + ez + S], Mn[t - ez + S]);
+                    const f2 d1 = f2sub(Pn[t + ez + S], Mc[t - ez + S]);
+                    if constexpr (EX != 0) {
+                        const f2 u = f2splat((float)(EX / len));
+                        acc[0][t][0] = f2fma(u, d0, acc[0][t][0]);
+                        acc[1][t][0] = f2fma(u, d1, acc[1][t][0]);
+                    }
+                    if constexpr (EY != 0) {
+                        const f2 u = f2splat((float)(EY / len));
+                        acc[0][t][1] = f2fma(u, d0, acc[0][t][1]);
+                        acc[1][t][1] = f2fma(u, d1, acc[1][t][1]);
+                    }
+                    if constexpr (ez != 0) {
+                        const f2 u = f2splat((float)(ez / len));
+                        acc[0][t][2] = f2fma(u, d0, acc[0][t][2]);
+                        acc[1][t][2] = f2fma(u, d1, acc[1][t][2]);
+                    }
+                }
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, TZ *(2 * S + 1)>{});
+    // the next column's row y takes this "+" row EY + 1, its row y + 1 this "-" row -EY
+    [&]<int... K>(std::integer_sequence<int, K...>) {
+        (
+            [&] {
+                if constexpr (y_plus_needs<S, TZ>(m | mn, K)) Pc[K] = Pn[K];
+                if constexpr (y_minus_needs<S, TZ>(m | mn, K)) Mc[K] = Mn[K];
+            }(),
+            ...);
+    }(std::make_integer_sequence<int, NK>{});
+}
+
+template <int S, int TZ, int TYT, int EX>
+__device__ __forceinline__ void y_chain(const f2 *const *sb, f2 (*acc)[TZ][3]) {
+    using Tl = ShellTileY<S, TZ, TYT>;
+    constexpr int NK = 2 * S + TZ;
+    constexpr int hi = col_eymax(S, EX);
+    constexpr int lo = EX == 0 ? 1 : -hi;
+    if constexpr (hi >= 0 && lo <= hi) {
+        constexpr unsigned m0 = col_mask(S, EX, lo);
+        f2 Pc[NK], Mc[NK];
+        // the first column: row y's "+" row lo, row y + 1's "-" row 1 - lo
+        [&]<int... K>(std::integer_sequence<int, K...>) {
+            (
+                [&] {
+                    if constexpr (y_plus_needs<S, TZ>(m0, K)) Pc[K] = sb[K][lo * Tl::BX + EX];
+                    if constexpr (y_minus_needs<S, TZ>(m0, K)) Mc[K] = sb[K][(1 - lo) * Tl::BX - EX];
+                }(),
+                ...);
+        }(std::make_integer_sequence<int, NK>{});
+        [&]<int... I>(std::integer_sequence<int, I...>) {
+            (y_column<S, TZ, TYT, EX, lo + I>(sb, Pc, Mc, acc), ...);
+        }(std::make_integer_sequence<int, hi - lo + 1>{});
+    }
+}
+
+template <int S, int TZ, int TYT, int... EX>
+__device__ __forceinline__ void y_all(const f2 *const *sb, f2 (*acc)[TZ][3], std::integer_sequence<int, EX...>) {
+    (y_chain<S, TZ, TYT, EX>(sb, acc), ...);
+}
+
+template <int S, int TZ, int TYT>
+__global__ void __launch_bounds__(32 * TYT, 1)
+    k_shell_force_yb(const __grid_constant__ CUtensorMap map_gn2, Grid g, int ox, const float *__restrict__ npad_a,
+                     const float *__restrict__ g_ab, float *__restrict__ Cout, float *__restrict__ Pout, float coef,
+                     int accumulate, int *err) {
+    using Tl = ShellTileY<S, TZ, TYT>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base = smem_align128(smem_raw);
+    const f2 *ring = reinterpret_cast<const f2 *>(base);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(base + Tl::R * Tl::SLOT_BYTES);
+    constexpr int SLOT = Tl::SLOT_BYTES / 8;
+    constexpr int NK = 2 * S + TZ;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int x0 = blockIdx.x * Tl::TX, y0 = blockIdx.y * Tl::TY, z0 = blockIdx.z * Tl::LZ;
+    const int zend = min(z0 + Tl::LZ, g.nz);
+    const int nsuper = (zend - z0 + TZ - 1) / TZ;
+    const int nplanes = nsuper * TZ + 2 * S;
+    const bool leader = (tx == 0 && ty == 0);
+    const int bx = x0 + g.H - S - ox;
+    const int by = y0 + g.H - S;
+    constexpr uint32_t tx_bytes = (uint32_t)Tl::PLANE * 8u;
+
+    if (leader) {
+        prefetch_tensormap(&map_gn2);
+        for (int r = 0; r < Tl::R; ++r) mbar_init(&bars[r], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int j) {  // plane j holds interior z = z0 - S + j
+        const int slot = j % Tl::R;
+        const int zp = z0 - S + j + g.H;
+        mbar_arrive_expect_tx(&bars[slot], tx_bytes);
+        tma_load_3d(base + slot * Tl::SLOT_BYTES, &map_gn2, bx, by, zp, &bars[slot]);
+    };
+    if (leader)
+        for (int j = 0; j < Tl::R && j < nplanes; ++j) issue(j);
+
+    const int x = x0 + tx;
+    const int yb = y0 + 2 * ty;  // this thread's rows yb and yb + 1
+    const int toff = (2 * ty + S) * Tl::BX + (tx + S + ox);
+    const float half = 0.5f;
+
+    for (int s = 0; s < nsuper; ++s) {
+        const int j0 = s * TZ;
+        for (int j = j0; j < j0 + NK; ++j)
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+        if (x < g.nx && yb < g.ny) {
+            // the epilogue's global loads are issued before the shell sum so their latency hides behind it
+            float pre[2][TZ], gr[2][TZ], old[2][TZ][3];
+            long long idx[2][TZ];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int t = 0; t < TZ; ++t) {
+                    const int y = min(yb + r, g.ny - 1);
+                    const int z = min(z0 + j0 + t, zend - 1);
+                    idx[r][t] = (long long)x + (long long)g.nx * ((long long)y + (long long)g.ny * z);
+                    pre[r][t] = coef * npad_a[pidx(g, x, y, z)];
+                    gr[r][t] = g_ab[idx[r][t]];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) old[r][t][c] = accumulate ? Cout[(long long)c * g.N + idx[r][t]] : 0.f;
+                }
+            const f2 *sb[NK];
+#pragma unroll
+            for (int k = 0; k < NK; ++k) sb[k] = ring + ((j0 + k) % Tl::R) * SLOT + toff;
+            f2 acc[2][TZ][3];
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int t = 0; t < TZ; ++t)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[r][t][c] = 0ull;
+            // centre column (0, 0, +-S): e^ = (0, 0, 1) for ez = +S
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+#pragma unroll
+                for (int t = 0; t < TZ; ++t)
+                    acc[r][t][2] = f2add(acc[r][t][2], f2sub(sb[t + 2 * S][r * Tl::BX], sb[t][r * Tl::BX]));
+            y_all<S, TZ, TYT>(sb, acc, std::make_integer_sequence<int, S + 1>{});
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (yb + r >= g.ny) continue;
+#pragma unroll
+                for (int t = 0; t < TZ; ++t) {
+                    if (z0 + j0 + t >= zend) continue;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float2 v = f2unpack(acc[r][t][c]);  // (sum over n_b, sum over g n_b)
+                        Cout[(long long)c * g.N + idx[r][t]] =
+                            old[r][t][c] + pre[r][t] * (half * gr[r][t] * v.x + half * v.y);
+                        if (Pout) Pout[(long long)c * g.N + idx[r][t]] = v.x;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        if (leader) {
+            fence_proxy_async_smem();
+            for (int j = j0 + Tl::R; j < j0 + Tl::R + TZ && j < nplanes; ++j) issue(j);
+        }
+    }
+}
+
+template <int S, int TZ, int TYT>
+cudaError_t launch_yb(const ShellLaunch &L, cudaStream_t st) {
+    using Tl = ShellTileY<S, TZ, TYT>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_shell_force_yb<S, TZ, TYT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             Tl::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const Grid &g = *L.grid;
+    dim3 block(Tl::TX, Tl::TYT, 1);
+    dim3 grid((g.nx + Tl::TX - 1) / Tl::TX, (g.ny + Tl::TY - 1) / Tl::TY, (g.nz + Tl::LZ - 1) / Tl::LZ);
+    const int ox = ((g.H - S) % Tl::A + Tl::A) % Tl::A;
+    k_shell_force_yb<S, TZ, TYT><<<grid, block, Tl::SMEM, st>>>(*L.map_gn, g, ox, (const float *)L.npad_a,
+                                                          (const float *)L.g_ab, (float *)L.Cout, (float *)L.Pout,
+                                                          (float)L.coef, L.accumulate, L.err);
+    return cudaGetLastError();
+}
+
 template <int S, int TZ, int TYB>
 cudaError_t launch_zb(const ShellLaunch &L, cudaStream_t st) {
     using Tl = ShellTileZ2<S, TZ, TYB>;
