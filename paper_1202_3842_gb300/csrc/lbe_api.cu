@@ -702,9 +702,8 @@ StepParams step_params(const lbe_ctx *c) {
     const bool euler = c->cfg.scheme == LBE_SD_EU || c->cfg.scheme == LBE_DD_EU;
     for (int a = 0; a < c->M; ++a) {
         double omega = 1.0 / (c->tau[a] - 0.5);
-        sp.sp[a].omega_eff = omega / (1.0 + 0.5 * omega);  // = 1/tau, also the Euler rate
-        sp.sp[a].inv = euler ? 1.0 : 1.0 / (1.0 + 0.5 * omega);
-        sp.sp[a].n0 = c->n0[a];
+        // omega_eff = 1/tau, also the Euler rate
+        species_const_set(sp.sp[a], omega / (1.0 + 0.5 * omega), euler ? 1.0 : 1.0 / (1.0 + 0.5 * omega), c->n0[a]);
     }
     return sp;
 }

@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     const int psize = sp.flux_axis == 0 ? g.ny * g.nz : (sp.flux_axis == 1 ? g.nx * g.nz : g.nx * g.ny);
 
     // this species' constants (selected, not indexed, so the parameter block stays in constant memory)
+    // (16-bit storage takes the float copies rounded on the host; the doubles are then unused)
     const double n0d = a == 0 ? sp.sp[0].n0 : sp.sp[1].n0;
     const double omd = a == 0 ? sp.sp[0].omega_eff : sp.sp[1].omega_eff;
     const double invd = a == 0 ? sp.sp[0].inv : sp.sp[1].inv;
@@ -57,7 +58,7 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
     NbrOff o{};
     if (fluid) {
         o = nbr_offsets(g, x, y, z);
-        const T n0 = (T)n0d;
+        const T n0 = sc_float<S, T> ? (T)(a == 0 ? sp.sp[0].n0_f : sp.sp[1].n0_f) : (T)n0d;
         const S *fb = src + pop_off(a, 0, 0, g.N);
         const S *gb = src + pop_off(a, 1, 0, g.N);
         // DEV: the populations as deviations from w_p n0 (f, gq below hold f - w_p n0, g - w_p n0)
@@ -141,10 +142,18 @@ __global__ void __launch_bounds__(NTP, sizeof(T) == 4 ? (M == 1 ? 4 : 3) : 1)
 #pragma unroll
     for (int c = 0; c < 3; ++c) X[c] = Cv[c] + nF[c];
     const T sf0 = (T)-3 * (X[0] * ua[0] + X[1] * ua[1] + X[2] * ua[2]);
-    const T om = (T)omd;
-    const T inv = (T)invd;
-    const T in0 = n0d > 0.0 ? (T)(1.0 / n0d) : (T)0;
-    const T n0s = (T)n0d;
+    T om, inv, in0, n0s;
+    if constexpr (sc_float<S, T>) {
+        om = a == 0 ? sp.sp[0].omega_eff_f : sp.sp[1].omega_eff_f;
+        inv = a == 0 ? sp.sp[0].inv_f : sp.sp[1].inv_f;
+        in0 = a == 0 ? sp.sp[0].in0_f : sp.sp[1].in0_f;
+        n0s = a == 0 ? sp.sp[0].n0_f : sp.sp[1].n0_f;
+    } else {
+        om = (T)omd;
+        inv = (T)invd;
+        in0 = n0d > 0.0 ? (T)(1.0 / n0d) : (T)0;
+        n0s = (T)n0d;
+    }
     S *fo = dst + pop_off(a, 0, 0, g.N) + i;
     S *go = dst + pop_off(a, 1, 0, g.N) + i;
     [&]<int... P>(std::integer_sequence<int, P...>) {

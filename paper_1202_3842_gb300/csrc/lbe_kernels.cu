@@ -23,6 +23,9 @@ constexpr int NT = 256;
 struct N0Vec {
     double v[MAXS];
 };
+struct N0VecF {  // the same rounded once on the host, read with 16-bit storage
+    float v[MAXS];
+};
 
 // ---------------------------------------------------------------------------
 // geometry
@@ -226,7 +229,8 @@ cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const
 // ---------------------------------------------------------------------------
 template <typename S, typename T, bool SOLID>
 __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ pop, const uint32_t *__restrict__ mask,
-                                                int M, N0Vec n0v, T *__restrict__ npad, int *err) {
+                                                int M, N0Vec n0v, N0VecF n0f, T *__restrict__ npad,
+                                                int *err) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.N) return;
     int x, y, z;
@@ -237,7 +241,11 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
         T n = (T)0;
         if (!(m & 1u)) {
             const S *fb = pop + pop_off(a, 0, 0, g.N);
-            const T n0 = (T)n0v.v[a];
+            T n0;
+            if constexpr (sc_float<S, T>)
+                n0 = n0f.v[a];
+            else
+                n0 = (T)n0v.v[a];
             // shifted storage: n = n0 + the sum of the deviations
             [&]<int... P>(std::integer_sequence<int, P...>) {
                 if constexpr (Store<S, T>::shifted)
@@ -259,11 +267,15 @@ cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_
     if (M == 1) return launch_density_pair(p, g, pop, mask, solid, M, n0, npad, err, st);
     unsigned nb = (unsigned)((g.N + NT - 1) / NT);
     N0Vec n0v;
-    for (int a = 0; a < MAXS; ++a) n0v.v[a] = a < M ? n0[a] : 0.0;
+    N0VecF n0f;
+    for (int a = 0; a < MAXS; ++a) {
+        n0v.v[a] = a < M ? n0[a] : 0.0;
+        n0f.v[a] = (float)n0v.v[a];
+    }
     if (solid) {
-        LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
+        LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, n0f, (T *)npad, err)));
     } else {
-        LBE_DISPATCH_PREC(p, (k_density<S, T, false><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, (T *)npad, err)));
+        LBE_DISPATCH_PREC(p, (k_density<S, T, false><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, n0f, (T *)npad, err)));
     }
     return cudaGetLastError();
 }
@@ -310,7 +322,7 @@ __device__ __forceinline__ void load_moments(const Grid &g, const S *__restrict_
     T ntot = 0, Jtot[3] = {0, 0, 0};
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        const T n0 = (T)sp.sp[a].n0;
+        const T n0 = sc_n0<S, T>(sp.sp[a]);
         T fl[Q], gl[Q];
         T *f = KEEP ? st.f[KEEP ? a : 0] : fl;
         T *gq = KEEP ? st.g[KEEP ? a : 0] : gl;
@@ -387,9 +399,9 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (M == 1 ? 3 : 2) : 1)
 #pragma unroll
         for (int c = 0; c < 3; ++c) X[c] = st.C[a][c] + st.nF[a][c];
         const T sf0 = (T)-3 * (X[0] * ua[0] + X[1] * ua[1] + X[2] * ua[2]);
-        const T om = (T)sp.sp[a].omega_eff;
-        const T inv = (T)sp.sp[a].inv;
-        const T in0 = sp.sp[a].n0 > 0.0 ? (T)(1.0 / sp.sp[a].n0) : (T)0;
+        const T om = sc_omega<S, T>(sp.sp[a]);
+        const T inv = sc_inv<S, T>(sp.sp[a]);
+        const T in0 = sc_in0<S, T>(sp.sp[a]);
         T fl[Q], gl[Q];
         const T *fa = st.f[0];
         const T *ga = st.g[0];
@@ -397,7 +409,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (M == 1 ? 3 : 2) : 1)
             fa = st.f[KEEP ? a : 0];
             ga = st.g[KEEP ? a : 0];
         } else {
-            pull_species<S, T, SOLID>(g, src, a, (T)sp.sp[a].n0, i, o, m, fl, gl);
+            pull_species<S, T, SOLID>(g, src, a, sc_n0<S, T>(sp.sp[a]), i, o, m, fl, gl);
             fa = fl;
             ga = gl;
         }
@@ -420,8 +432,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? (M == 1 ? 3 : 2) : 1)
                     const T fs = fa[P] + om * (feq - fa[P]) + inv * Sf;
                     const T gs = ga[P] + om * (geq - ga[P]) + inv * Sg;
                     constexpr T iw = (T)(1.0 / wq(P));
-                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * (T)sp.sp[a].n0, iw * in0);
-                    Store<S, T>::store(go + (long long)P * g.N, gs, w * (T)sp.sp[a].n0, iw * in0);
+                    Store<S, T>::store(fo + (long long)P * g.N, fs, w * sc_n0<S, T>(sp.sp[a]), iw * in0);
+                    Store<S, T>::store(go + (long long)P * g.N, gs, w * sc_n0<S, T>(sp.sp[a]), iw * in0);
                 }(),
                 ...);
         }(std::make_integer_sequence<int, Q>{});

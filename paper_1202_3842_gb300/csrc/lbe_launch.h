@@ -17,12 +17,49 @@ enum class Prec : int { F64 = 0, F32 = 1, BF16 = 2, F16 = 3 };
 inline int prec_bytes(Prec p) { return p == Prec::F64 ? 8 : (p == Prec::F32 ? 4 : 2); }
 inline bool prec_fp64(Prec p) { return p == Prec::F64; }
 
-// Per-species constants of the collision.
+// Per-species constants of the collision, in FP64 and rounded once to FP32 on the host.  Kernels with
+// 16-bit storage read the float copies (their store needs 1/n0, which a thread would otherwise divide
+// in FP64, at GB300's low FP64 rate).  Kernels with FP32 storage convert the doubles themselves, which
+// compiled to fewer spills at the collide's register cap.
 struct SpeciesConst {
     double omega_eff;  // omega h / (1 + omega h / 2) = 1/tau
     double inv;        // h / (1 + omega h / 2)
-    double n0;         // reference density of the shifted 16-bit storage
+    double n0;         // reference density of the shifted storage
+    double in0;        // 1 / n0 (0 if n0 is 0)
+    float omega_eff_f, inv_f, n0_f, in0_f;
 };
+
+inline void species_const_set(SpeciesConst &s, double omega_eff, double inv, double n0) {
+    s.omega_eff = omega_eff;
+    s.inv = inv;
+    s.n0 = n0;
+    s.in0 = n0 > 0.0 ? 1.0 / n0 : 0.0;
+    s.omega_eff_f = (float)s.omega_eff;
+    s.inv_f = (float)s.inv;
+    s.n0_f = (float)s.n0;
+    s.in0_f = (float)s.in0;
+}
+
+// Whether a kernel with storage type S and arithmetic type T reads the float copies, and the constants
+// in T either way.
+template <typename S, typename T>
+inline constexpr bool sc_float = sizeof(T) == 4 && sizeof(S) == 2;
+template <typename S, typename T>
+__host__ __device__ __forceinline__ T sc_omega(const SpeciesConst &s) {
+    if constexpr (sc_float<S, T>) return s.omega_eff_f; else return (T)s.omega_eff;
+}
+template <typename S, typename T>
+__host__ __device__ __forceinline__ T sc_inv(const SpeciesConst &s) {
+    if constexpr (sc_float<S, T>) return s.inv_f; else return (T)s.inv;
+}
+template <typename S, typename T>
+__host__ __device__ __forceinline__ T sc_n0(const SpeciesConst &s) {
+    if constexpr (sc_float<S, T>) return s.n0_f; else return (T)s.n0;
+}
+template <typename S, typename T>
+__host__ __device__ __forceinline__ T sc_in0(const SpeciesConst &s) {
+    if constexpr (sc_float<S, T>) return s.in0_f; else return s.n0 > 0.0 ? (T)(1.0 / s.n0) : (T)0;
+}
 
 struct StepParams {
     int M;

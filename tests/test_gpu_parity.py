@@ -97,13 +97,18 @@ def test_stage_parity_fp64(shape, sig, shell):
 
 
 @pytest.mark.parametrize("shell", ["direct", "spectral"])
-@pytest.mark.parametrize("sig", [(1.0,), (2.0, 4.0), (4.0, 6.0), (6.0, 8.0), (8.0,), (3.0, 5.0)])
-def test_stage_parity_fp32_every_pair_diameter(sig, shell):
-    """K1-K3 of one FP32 state against the oracle for pair diameters 1 to 8 (the FP32 shell tiles: three
-    outputs per thread along z up to 6, two at 7, one at 8) and both contact paths (compile-time balls for
-    sigma 4/6, runtime rows otherwise, up to ball radius 4).  Tolerance: 1e-5 of the largest value of each
-    field (FP32 sums over up to 762 shell points)."""
-    w, arr = case_channel((40, 22, 20), sig, 0.2, (1.0,) * len(sig), 10, 8)
+@pytest.mark.parametrize("sig,shape", [((1.0,), (40, 22, 20)), ((2.0, 4.0), (40, 22, 20)), ((4.0, 6.0), (40, 22, 20)),
+                                       ((6.0, 8.0), (40, 22, 20)), ((8.0,), (40, 22, 20)), ((3.0, 5.0), (40, 22, 20)),
+                                       ((4.0, 6.0), (70, 37, 41))])
+def test_stage_parity_fp32_every_pair_diameter(sig, shape, shell):
+    """K1-K3 of one FP32 state against the oracle for pair diameters 1 to 8 and both contact paths
+    (compile-time balls for sigma 4/6, runtime rows otherwise, up to ball radius 4).  The FP32 shell
+    tiles: two rows along y and three planes along z per thread for diameters 4 to 6 (32 x 16 outputs
+    per plane, 18 planes per thread block); three outputs along z for 1 to 3, two at 7, one at 8.  Both
+    lattices end in a partial tile along x, y and z; 70 x 37 x 41 spans three tiles along y and three
+    z-blocks.  Tolerance: 1e-5 of the largest value of each field (FP32 sums over up to 762 shell
+    points)."""
+    w, arr = case_channel(shape, sig, 0.2, (1.0,) * len(sig), 10, 8)
     rng = np.random.default_rng(9)
     fl = arr["solid"] == 0
     arr["n"] = arr["n"] * (1.0 + 0.2 * (rng.random(arr["n"].shape) - 0.5)) * fl[None, :]
