@@ -23,6 +23,9 @@ constexpr int NT = 256;
 struct N0Vec {
     double v[MAXS];
 };
+#ifndef LBE_K1_TWO
+#define LBE_K1_TWO 1  // two species: K1 instantiated for exactly two, every load issued before the sums
+#endif
 struct N0VecF {  // the same rounded once on the host, read with 16-bit storage
     float v[MAXS];
 };
@@ -227,7 +230,7 @@ cudaError_t launch_stream_out(Prec p, const Grid &g, const uint32_t *mask, const
 // K1: density n^a(r) = sum_p f~_p(r) (streamed), 0 on solid nodes, written to
 // the padded stencil field with its periodic images.
 // ---------------------------------------------------------------------------
-template <typename S, typename T, bool SOLID>
+template <typename S, typename T, bool SOLID, int MC>
 __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ pop, const uint32_t *__restrict__ mask,
                                                 int M, N0Vec n0v, N0VecF n0f, T *__restrict__ npad,
                                                 int *err) {
@@ -237,26 +240,54 @@ __global__ void __launch_bounds__(NT) k_density(Grid g, const S *__restrict__ po
     node_xyz(g, i, x, y, z);
     const uint32_t m = SOLID ? mask[i] : 0u;
     const NbrOff o = nbr_offsets(g, x, y, z);  // (without solids every axis is periodic)
-    for (int a = 0; a < M; ++a) {
-        T n = (T)0;
-        if (!(m & 1u)) {
-            const S *fb = pop + pop_off(a, 0, 0, g.N);
-            T n0;
-            if constexpr (sc_float<S, T>)
-                n0 = n0f.v[a];
+    auto n0_of = [&](int a) -> T {
+        if constexpr (sc_float<S, T>)
+            return n0f.v[a];
+        else
+            return (T)n0v.v[a];
+    };
+    // one species' pulled populations (shifted storage: their deviations from w_p n0)
+    auto pull_all = [&](int a, T *v) {
+        const S *fb = pop + pop_off(a, 0, 0, g.N);
+        const T n0 = n0_of(a);
+        [&]<int... P>(std::integer_sequence<int, P...>) {
+            if constexpr (Store<S, T>::shifted)
+                ((v[P] = pull_dev<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
             else
-                n0 = (T)n0v.v[a];
-            // shifted storage: n = n0 + the sum of the deviations
-            [&]<int... P>(std::integer_sequence<int, P...>) {
-                if constexpr (Store<S, T>::shifted)
-                    ((n += pull_dev<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
-                else
-                    ((n += pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
-            }(std::make_integer_sequence<int, Q>{});
-            if constexpr (Store<S, T>::shifted) n = n0 + n;
-            if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
+                ((v[P] = pull<S, T, P, SOLID>(fb, g.N, i, o, m, n0)), ...);
+        }(std::make_integer_sequence<int, Q>{});
+    };
+    // n = n0 + the sum of the deviations (shifted storage), the sum itself otherwise
+    auto finish = [&](int a, const T *v) -> T {
+        T n = (T)0;
+#pragma unroll
+        for (int p = 0; p < Q; ++p) n += v[p];
+        if constexpr (Store<S, T>::shifted) n = n0_of(a) + n;
+        if (!(n >= (T)0) || !isfinite(n)) atomicOr(err, ERR_DENSITY);
+        return n;
+    };
+    if constexpr (MC == 2) {
+        // two species: all 38 loads issue before either sum
+        T n[2] = {(T)0, (T)0};
+        if (!(m & 1u)) {
+            T v0[Q], v1[Q];
+            pull_all(0, v0);
+            pull_all(1, v1);
+            n[0] = finish(0, v0);
+            n[1] = finish(1, v1);
         }
-        write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);
+        write_padded<T>(g, npad, x, y, z, n[0]);
+        write_padded<T>(g, npad + g.P, x, y, z, n[1]);
+    } else {
+        for (int a = 0; a < M; ++a) {
+            T n = (T)0;
+            if (!(m & 1u)) {
+                T v[Q];
+                pull_all(a, v);
+                n = finish(a, v);
+            }
+            write_padded<T>(g, npad + (long long)a * g.P, x, y, z, n);
+        }
     }
 }
 
@@ -272,11 +303,20 @@ cudaError_t launch_density(Prec p, const Grid &g, const void *pop, const uint32_
         n0v.v[a] = a < M ? n0[a] : 0.0;
         n0f.v[a] = (float)n0v.v[a];
     }
-    if (solid) {
-        LBE_DISPATCH_PREC(p, (k_density<S, T, true><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, n0f, (T *)npad, err)));
+#define LBE_K1(SOL, MC) \
+    LBE_DISPATCH_PREC(p, (k_density<S, T, SOL, MC><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, n0f, (T *)npad, err)))
+    if (M == 2 && LBE_K1_TWO) {
+        if (solid) {
+            LBE_K1(true, 2);
+        } else {
+            LBE_K1(false, 2);
+        }
+    } else if (solid) {
+        LBE_K1(true, 0);
     } else {
-        LBE_DISPATCH_PREC(p, (k_density<S, T, false><<<nb, NT, 0, st>>>(g, (const S *)pop, mask, M, n0v, n0f, (T *)npad, err)));
+        LBE_K1(false, 0);
     }
+#undef LBE_K1
     return cudaGetLastError();
 }
 
