@@ -13,14 +13,15 @@
 // shared-memory ring by TMA (cp.async.bulk.tensor, 2-D boxes of
 // (32 + 2S) x (TY + 2S) per plane, completion on an mbarrier per ring slot).
 // The plain kernel (FP64) reads the padded density n_b and the padded product
-// g_ab*n_b as two planes and gives each thread one output per plane.  The
-// z-blocked kernel (FP32) reads the interleaved pair (n_b, g_ab n_b) as one
-// 8-byte element per node, gives each thread TZ outputs along z, reuses every
-// shared-memory read across them, and sums both fields with packed f32x2
-// instructions.  The shell
-// offsets and unit vectors are compile-time immediates.  When Pout is given,
-// the kernels also store P = sum_e e^ n_b(r+e) of the pair ([3][N]), which the
-// discrete adjoint needs.
+// g_ab*n_b as two planes and gives each thread one output per plane.  The FP32
+// kernels read the interleaved pair (n_b, g_ab n_b) as one 8-byte element per
+// node and sum both fields with packed f32x2 instructions: the z-blocked one
+// gives each thread TZ outputs along z and reuses every shared-memory read
+// across them; the y-blocked one (pair diameters 4 to 6) gives each thread two
+// output rows as well and carries shell rows in registers from one column of
+// the half shell to the next.  The shell offsets and unit vectors are
+// compile-time immediates.  When Pout is given, the kernels also store
+// P = sum_e e^ n_b(r+e) of the pair ([3][N]), which the discrete adjoint needs.
 #pragma once
 #include <utility>
 
