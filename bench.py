@@ -485,6 +485,41 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
     return out
 
 
+def step_roofline(w, prec, N, M, sb, ms_step, stage_ms, kernels, hbm, fp_peak_tflops, shell_method):
+    """The whole step against its bounds.
+    - roof_max_ms: max(bytes / HBM, flops / FP peak) over the step's algorithmic totals.  Bytes: the
+      populations (76 per node and species) alone and with C, F and n (7 words per node and species) and
+      the link mask (4 B per node).  Flops: the shell sums (shell_flops_per_node per ordered pair), the
+      collision (K4_FLOPS_PER_NODE_SPECIES per node and species) and the ball sums of the contact values
+      (one add per ball point).  Computed for the direct shell form; the spectral form's transforms are
+      not counted here.
+    - stage_roof_sum_ms: the sum over stages of each stage's own bound (stage time x its roofline
+      fraction), since the stages run one after another; the stages without a fraction (the flux
+      reduction) are left out."""
+    rb = 8 if prec == "fp64" else 4
+    pop_bytes = N * M * 4 * QPOP * sb
+    full_bytes = pop_bytes + N * M * 7 * rb + N * 4
+    out = {"population_bytes_per_step": pop_bytes, "full_bytes_per_step": full_bytes,
+           "population_frac_of_measured_hbm": pop_bytes / (ms_step * 1e-3) / 1e9 / hbm,
+           "full_frac_of_measured_hbm": full_bytes / (ms_step * 1e-3) / 1e9 / hbm}
+    if shell_method == "direct" and fp_peak_tflops:
+        S_list = [int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]
+        flops = N * (sum(shell_flops_per_node(S) for S in S_list) + M * K4_FLOPS_PER_NODE_SPECIES
+                     + sum(ball_count(0.5 * s_) for s_ in w["sigma"] if s_ > 0))
+        t_b = full_bytes / (hbm * 1e9) * 1e3
+        t_f = flops / (fp_peak_tflops * 1e12) * 1e3
+        out.update({"flops_per_step": flops, "roof_bytes_ms": t_b, "roof_flops_ms": t_f,
+                    "roof_max_ms": max(t_b, t_f), "frac_of_roof_max": max(t_b, t_f) / ms_step,
+                    "bound": "flops" if t_f >= t_b else "bytes"})
+    parts = {k: stage_ms[k] * kernels[k]["frac"] for k in ("density", "contact", "shell", "collide")
+             if k in stage_ms and k in kernels and kernels[k].get("frac")}
+    if parts:
+        out["stage_roof_ms"] = parts
+        out["stage_roof_sum_ms"] = sum(parts.values())
+        out["frac_of_stage_roof_sum"] = sum(parts.values()) / ms_step
+    return out
+
+
 def spectral_grid(w):
     """Grid of the spectral form: the lattice along periodic axes, the next 2-3-5-7 size of at least
     n + S_max along closed ones (S_max the largest pair diameter)."""
@@ -618,6 +653,11 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
            "population_gbs_whole_step": step_bytes / (ms_step * 1e-3) / 1e9,
            "population_gbs_whole_step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
            "kernels": res_kernels,
+           "step_roofline": step_roofline(w, prec, N, M, sb, ms_step, {k: v[0] / steps for k, v in stages.items()},
+                                          res_kernels, hbm,
+                                          (sms * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0))
+                                           * 1e6 / 1e12) if prec != "fp64" else FP64_NOMINAL_TFLOPS,
+                                          shell_method),
            "gpu_launches": launches, "state_after": state, "sm_count": sms,
            "max_u_over_vT_after": umax / math.sqrt(1.0 / 3.0)}
     if clocks is not None:
@@ -774,8 +814,8 @@ def run_ours(args):
               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE[args.prec],
               "data": "synthetic (seeded inputs of the workload's shape and distribution)"}
     for k in ("config", "roofline", "mlups_nodes", "kernels", "stage_ms_per_step", "population_gbs_whole_step",
-              "population_gbs_whole_step_frac", "gpu_launches", "clocks", "state_after", "max_u_over_vT_after",
-              "sm_count"):
+              "population_gbs_whole_step_frac", "step_roofline", "gpu_launches", "clocks", "state_after",
+              "max_u_over_vT_after", "sm_count"):
         result[k] = core.get(k)
 
     # end to end through the C ABI with host buffers: the timed region holds the host->device copy of the

@@ -70,3 +70,30 @@ def test_fp64_collide_is_reported_against_the_fp64_rate():
 def test_ball_counts_match_the_contact_balls():
     # the oracle's ball lists, counted independently
     assert [bench.ball_count(r) for r in (0.0, 1.5, 2.0, 2.5, 3.0)] == [1, 19, 33, 81, 123]
+
+
+def test_step_roofline_totals_and_stage_sum():
+    """The step's bytes and flops from their per-node counts, the max-roof against the two peaks, and
+    the sum of the stages' own bounds (stage time x fraction)."""
+    N, M = 1000, 2
+    w = {"sigma": [4.0, 6.0], "shape": (10, 10, 10), "periodic": (1, 0, 0)}
+    stage_ms = {"density": 0.2, "contact": 0.25, "shell": 1.5, "collide": 0.9, "flux": 0.02}
+    kernels = {"density": {"frac": 0.8}, "contact": {"frac": 0.5}, "shell": {"frac": 0.6},
+               "collide": {"frac": 0.85}}
+    r = bench.step_roofline(w, "fp32", N, M, 4, 3.0, stage_ms, kernels, 1000.0, 80.0, "direct")
+    assert r["population_bytes_per_step"] == N * M * 4 * 19 * 4
+    assert r["full_bytes_per_step"] == N * M * (304 + 7 * 4) + N * 4
+    S_list = [4, 5, 5, 6]
+    flops = N * (sum(bench.shell_flops_per_node(S) for S in S_list) + M * bench.K4_FLOPS_PER_NODE_SPECIES
+                 + 33 + 123)
+    assert r["flops_per_step"] == flops
+    t_b = r["full_bytes_per_step"] / 1000e9 * 1e3
+    t_f = flops / 80e12 * 1e3
+    assert abs(r["roof_max_ms"] - max(t_b, t_f)) < 1e-15
+    assert abs(r["frac_of_roof_max"] - max(t_b, t_f) / 3.0) < 1e-15
+    want = 0.2 * 0.8 + 0.25 * 0.5 + 1.5 * 0.6 + 0.9 * 0.85
+    assert abs(r["stage_roof_sum_ms"] - want) < 1e-12
+    assert "flux" not in r["stage_roof_ms"]
+    # the spectral form: no flops roof, the stage sum still
+    r2 = bench.step_roofline(w, "fp32", N, M, 4, 3.0, stage_ms, kernels, 1000.0, 80.0, "spectral")
+    assert "roof_max_ms" not in r2 and abs(r2["stage_roof_sum_ms"] - want) < 1e-12
