@@ -416,6 +416,7 @@ def fft_size(n):
 
 
 def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_method):
+    # roof: the shell stage's roofline (shell_roofline), or None
     """Each stage kernel against its own bound, from the live per-stage event times.
     K1 (HBM): reads 19 f~ and writes one padded density per node and species.
     K4: reads and writes f~ and g~ (76 populations) per node and species; HBM bound with 32- and 16-bit
@@ -423,7 +424,8 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
     of K4_FLOPS_PER_NODE_SPECIES flops per node and species against the nominal FP64 rate.
     K2, stencil form: sum_b |B_b| shared-memory loads of the padded densities per node, against the
     shared-memory load bandwidth (32 banks x 4 B per clock per SM); in spectral form its fields through
-    HBM.  K3 is the roofline of the dominant-kernel entry when it dominates."""
+    HBM.  K3: the shell stage's roofline in the form in use (stencil: algorithmic flops against the FP32
+    FMA peak; spectral: its fields through HBM, or FP64 transform flops)."""
     rb = 8 if prec == "fp64" else 4
     out = {}
     name = w.get("name", "")
@@ -479,9 +481,14 @@ def kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms, clk, shell_metho
                               "achieved_gbs": b / t / 1e9, "peak_gbs": hbm, "frac": b / t / 1e9 / hbm,
                               "frac_of_measured_hbm": b / t / 1e9 / hbm, "fft_grid": L, "peak_source": hbm_src,
                               "traffic": traffic_for("contact_spectral", name, prec)}
-    if "shell" in stages and roof.get("kernel", "").startswith("k_shell_force"):
-        out["shell"] = {"bound": roof["bound"], "achieved_tflops": roof["achieved"], "peak_tflops": roof["peak"],
-                        "frac": roof["frac"], "peak_source": roof.get("peak_source"), "traffic": roof.get("traffic")}
+    if "shell" in stages and roof and roof.get("frac") is not None:
+        e = {"bound": roof["bound"], "frac": roof["frac"], "avg_launch_ms": roof.get("avg_launch_ms"),
+             "peak_source": roof.get("peak_source"), "traffic": roof.get("traffic")}
+        if roof.get("unit") == "GB/s":
+            e.update({"achieved_gbs": roof["achieved"], "peak_gbs": roof["peak"]})
+        else:
+            e.update({"achieved_tflops": roof["achieved"], "peak_tflops": roof["peak"]})
+        out["shell"] = e
     return out
 
 
@@ -518,6 +525,72 @@ def step_roofline(w, prec, N, M, sb, ms_step, stage_ms, kernels, hbm, fp_peak_tf
         out["stage_roof_sum_ms"] = sum(parts.values())
         out["frac_of_stage_roof_sum"] = sum(parts.values()) / ms_step
     return out
+
+
+def collide_roofline(N, M, sb, stage, peaks, peaks_kind, wname, prec):
+    """K4 as the dominant kernel: populations f~ and g~ read and written, against the copy bandwidth."""
+    ms, n = stage
+    per_launch_ms = ms / max(n, 1)
+    alg = N * M * 4 * QPOP * sb
+    achieved = alg / (per_launch_ms * 1e-3) / 1e9
+    peak = float(peaks["hbm_gbs"])
+    kname = "k_collide_pair" if M <= 2 else "k_collide"
+    return {"kernel": kname + " (K4 fused moments + DD-TR collision + streaming)", "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic_for("collide", wname, prec), "algorithmic_bytes_per_launch": alg,
+            "launches": n, "avg_launch_ms": per_launch_ms,
+            "peak_source": peaks_kind + " hbm_gbs (STREAM-style copy)"}
+
+
+def shell_roofline(w, prec, N, M, stage, peaks, peaks_kind, sms, wname, shell_method):
+    """K3 from the shell stage's own time, in the form in use."""
+    ms, n = stage
+    per_launch_ms = ms / max(n, 1)
+    dom_n = n
+    if shell_method == "spectral":
+        # The shell stage of the spectral form: the M^2 fields g n transformed forward, the 3 M^2 + 3 M
+        # force spectra back, the multiply and combine kernels (the density transform and the ball
+        # averages belong to the contact stage).  FP64: bound by the FP64 rate, counted as 2.5 L log2 L
+        # flops per real transform (half a complex transform of that size).  FP32: bound by HBM, counted
+        # as one read and one write of every transformed field plus the pointwise kernels' fields, each
+        # touched once.
+        L = spectral_grid(w)
+        Lr = L[0] * L[1] * L[2]
+        Lc = (L[0] // 2 + 1) * L[1] * L[2]
+        nf, ni, nS = M * M, 3 * M * M + 3 * M, len(set(S for S in [
+            int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]))
+        common = {"kernel": "K3 spectral (cuFFT transforms + k_spec_embed/multiply/combine)",
+                  "traffic": traffic_for("shell_spectral", wname, prec),
+                  "fft_grid": L, "launches": dom_n, "avg_launch_ms": per_launch_ms}
+        if prec == "fp64":
+            flops = (nf + ni) * 2.5 * Lr * math.log2(Lr)
+            achieved = flops / (per_launch_ms * 1e-3) / 1e12
+            roof = dict(common, bound="alu", achieved=achieved, peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
+                        frac=achieved / FP64_NOMINAL_TFLOPS, algorithmic_flops_per_launch=flops,
+                        peak_source="FP64 nominal vector rate of the part")
+        else:
+            rb = 4
+            byts = ((nf + ni) * (rb * Lr + 2 * rb * Lc)                 # transforms: read + write once
+                    + Lc * (2 * rb * (M + nf) + rb * 3 * nS + 2 * rb * ni)  # multiply (n^ and (g n)^ in)
+                    + ni * rb * Lr + (M + M * M + 3 * M) * rb * N)        # combine
+            achieved = byts / (per_launch_ms * 1e-3) / 1e9
+            peak = float(peaks["hbm_gbs"])
+            roof = dict(common, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
+                        algorithmic_bytes_per_launch=byts, peak_source=peaks_kind + " hbm_gbs (STREAM-style copy)")
+    else:
+        S_list = [int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]
+        flops = sum(shell_flops_per_node(S) for S in S_list) * N
+        per_launch_flops = flops / len(S_list)
+        achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
+        clk = float(peaks.get("sm_max_mhz", 2070.0))
+        peak = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12 if prec != "fp64" else None
+        roof = {"kernel": "k_shell_force (K3 mean-field shell force)", "bound": "alu", "achieved": achieved,
+                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "traffic": traffic_for("shell", wname, prec), "algorithmic_flops_per_launch": per_launch_flops,
+                "launches": dom_n, "avg_launch_ms": per_launch_ms,
+                "peak_source": "FP32 FMA: %d SMs (the device's multiprocessor count) x 128 lanes x 2 flop x "
+                               "%.0f MHz (max SM clock)" % (sms, clk)}
+    return roof
 
 
 def spectral_grid(w):
@@ -581,66 +654,15 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     ms_step = ms / steps
     value = replica_value(world, N, M, steps, ms * 1e-3)
 
-    dom = max(stages, key=lambda k: stages[k][0])
-    dom_ms, dom_n = stages[dom]
-    per_launch_ms = dom_ms / max(dom_n, 1)
     sb = STORE_BYTES[prec]
-    if dom == "collide":
-        alg = N * M * 4 * QPOP * sb  # populations f~ and g~ read + written
-        achieved = alg / (per_launch_ms * 1e-3) / 1e9
-        peak = float(peaks["hbm_gbs"])
-        kname = "k_collide_pair" if M <= 2 else "k_collide"
-        roof = {"kernel": kname + " (K4 fused moments + DD-TR collision + streaming)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic_for("collide", wname, prec), "algorithmic_bytes_per_launch": alg,
-                "launches": dom_n, "avg_launch_ms": per_launch_ms,
-                "peak_source": peaks_kind + " hbm_gbs (STREAM-style copy)"}
-    elif shell_method == "spectral":
-        # The shell stage of the spectral form: the M^2 fields g n transformed forward, the 3 M^2 + 3 M
-        # force spectra back, the multiply and combine kernels (the density transform and the ball
-        # averages belong to the contact stage).  FP64: bound by the FP64 rate, counted as 2.5 L log2 L
-        # flops per real transform (half a complex transform of that size).  FP32: bound by HBM, counted
-        # as one read and one write of every transformed field plus the pointwise kernels' fields, each
-        # touched once.
-        L = spectral_grid(w)
-        Lr = L[0] * L[1] * L[2]
-        Lc = (L[0] // 2 + 1) * L[1] * L[2]
-        nf, ni, nS = M * M, 3 * M * M + 3 * M, len(set(S for S in [
-            int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]))
-        common = {"kernel": "K3 spectral (cuFFT transforms + k_spec_embed/multiply/combine)",
-                  "traffic": traffic_for("shell_spectral", wname, prec),
-                  "fft_grid": L, "launches": dom_n, "avg_launch_ms": per_launch_ms}
-        if prec == "fp64":
-            flops = (nf + ni) * 2.5 * Lr * math.log2(Lr)
-            achieved = flops / (per_launch_ms * 1e-3) / 1e12
-            roof = dict(common, bound="alu", achieved=achieved, peak=FP64_NOMINAL_TFLOPS, unit="TFLOP/s",
-                        frac=achieved / FP64_NOMINAL_TFLOPS, algorithmic_flops_per_launch=flops,
-                        peak_source="FP64 nominal vector rate of the part")
-        else:
-            rb = 4
-            byts = ((nf + ni) * (rb * Lr + 2 * rb * Lc)                 # transforms: read + write once
-                    + Lc * (2 * rb * (M + nf) + rb * 3 * nS + 2 * rb * ni)  # multiply (n^ and (g n)^ in)
-                    + ni * rb * Lr + (M + M * M + 3 * M) * rb * N)        # combine
-            achieved = byts / (per_launch_ms * 1e-3) / 1e9
-            peak = float(peaks["hbm_gbs"])
-            roof = dict(common, bound="hbm", achieved=achieved, peak=peak, unit="GB/s", frac=achieved / peak,
-                        algorithmic_bytes_per_launch=byts, peak_source=peaks_kind + " hbm_gbs (STREAM-style copy)")
-    else:
-        S_list = [int(round(0.5 * (w["sigma"][a] + w["sigma"][b]))) for a in range(M) for b in range(M)]
-        flops = sum(shell_flops_per_node(S) for S in S_list) * N
-        per_launch_flops = flops / len(S_list)
-        achieved = per_launch_flops / (per_launch_ms * 1e-3) / 1e12
-        clk = float(peaks.get("sm_max_mhz", 2070.0))
-        peak = sms * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12 if prec != "fp64" else None
-        roof = {"kernel": "k_shell_force (K3 mean-field shell force)", "bound": "alu", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
-                "traffic": traffic_for("shell", wname, prec), "algorithmic_flops_per_launch": per_launch_flops,
-                "launches": dom_n, "avg_launch_ms": per_launch_ms,
-                "peak_source": "FP32 FMA: %d SMs (the device's multiprocessor count) x 128 lanes x 2 flop x "
-                               "%.0f MHz (max SM clock)" % (sms, clk)}
+    dom = max(stages, key=lambda k: stages[k][0])
+    shell_roof = (shell_roofline(w, prec, N, M, stages["shell"], peaks, peaks_kind, sms, wname, shell_method)
+                  if "shell" in stages else None)
+    roof = collide_roofline(N, M, sb, stages["collide"], peaks, peaks_kind, wname, prec) \
+        if dom == "collide" else shell_roof
     step_bytes = N * M * 4 * QPOP * sb
     hbm = float(peaks["hbm_gbs"])
-    res_kernels = kernel_rooflines(stages, w, prec, N, M, sb, hbm, roof, sms,
+    res_kernels = kernel_rooflines(stages, w, prec, N, M, sb, hbm, shell_roof, sms,
                                    float(peaks.get("sm_max_mhz", 2070.0)), shell_method)
     res = {"value": value, "ms_per_step": ms_step, "steps": steps, "warmup": warmup,
            "mlups_nodes": value / M,

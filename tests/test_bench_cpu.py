@@ -38,7 +38,7 @@ def test_kernel_rooflines_use_the_algorithmic_bytes():
     N, M = 1000, 2
     stages = {"density": (2.0, 4), "collide": (8.0, 4), "contact": (1.0, 4)}
     w = {"sigma": [4.0, 6.0], "shape": (10, 10, 10), "periodic": (1, 0, 0)}
-    out = bench.kernel_rooflines(stages, w, "fp32", N, M, 4, 1000.0, {"bound": "hbm"}, 152, 2070.0, "direct")
+    out = bench.kernel_rooflines(stages, w, "fp32", N, M, 4, 1000.0, None, 152, 2070.0, "direct")
     assert out["collide"]["algorithmic_bytes_per_launch"] == N * M * 4 * 19 * 4
     assert out["collide"]["bound"] == "hbm"
     assert out["density"]["algorithmic_bytes_per_launch"] == N * M * (19 * 4 + 4)
@@ -59,7 +59,7 @@ def test_fp64_collide_is_reported_against_the_fp64_rate():
     N, M = 1000, 2
     stages = {"collide": (8.0, 4)}
     w = {"sigma": [4.0, 6.0], "shape": (10, 10, 10), "periodic": (1, 1, 1)}
-    out = bench.kernel_rooflines(stages, w, "fp64", N, M, 8, 1000.0, {"bound": "alu"}, 152, 2070.0, "spectral")
+    out = bench.kernel_rooflines(stages, w, "fp64", N, M, 8, 1000.0, None, 152, 2070.0, "spectral")
     c = out["collide"]
     assert c["bound"] == "alu"
     assert c["algorithmic_flops_per_launch"] == N * M * bench.K4_FLOPS_PER_NODE_SPECIES
@@ -97,3 +97,23 @@ def test_step_roofline_totals_and_stage_sum():
     # the spectral form: no flops roof, the stage sum still
     r2 = bench.step_roofline(w, "fp32", N, M, 4, 3.0, stage_ms, kernels, 1000.0, 80.0, "spectral")
     assert "roof_max_ms" not in r2 and abs(r2["stage_roof_sum_ms"] - want) < 1e-12
+
+
+def test_shell_roofline_in_both_forms_and_its_kernels_entry():
+    """K3's roofline comes from the shell stage's own time: the stencil against the FP32 FMA peak, the
+    spectral form against the copy bandwidth (FP32), and the kernels table carries it either way."""
+    N, M = 1000, 2
+    w = {"sigma": [4.0, 6.0], "shape": (10, 10, 10), "periodic": (1, 0, 0)}
+    peaks = {"hbm_gbs": 1000.0, "sm_max_mhz": 2070.0}
+    r = bench.shell_roofline(w, "fp32", N, M, (8.0, 16), peaks, "measured", 152, "x", "direct")
+    flops = sum(bench.shell_flops_per_node(S) for S in (4, 5, 5, 6)) * N / 4
+    assert r["bound"] == "alu" and abs(r["avg_launch_ms"] - 0.5) < 1e-12
+    assert abs(r["achieved"] - flops / 0.5e-3 / 1e12) < 1e-12
+    assert abs(r["peak"] - 152 * 128 * 2 * 2070e6 / 1e12) < 1e-9
+    rs = bench.shell_roofline(w, "fp32", N, M, (8.0, 4), peaks, "measured", 152, "x", "spectral")
+    assert rs["bound"] == "hbm" and rs["unit"] == "GB/s"
+    for roof, key in ((r, "achieved_tflops"), (rs, "achieved_gbs")):
+        out = bench.kernel_rooflines({"shell": (8.0, 16)}, w, "fp32", N, M, 4, 1000.0, roof, 152, 2070.0, "direct")
+        assert out["shell"]["frac"] == roof["frac"] and key in out["shell"]
+    c = bench.collide_roofline(N, M, 4, (4.0, 4), peaks, "measured", "x", "fp32")
+    assert c["algorithmic_bytes_per_launch"] == N * M * 304 and abs(c["avg_launch_ms"] - 1.0) < 1e-12
