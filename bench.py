@@ -49,6 +49,7 @@ QPOP = 19
 # velocities and the isotropic terms 57, and per population 36 (t1 7, f_eq and g_eq 4, S_f 6, S_g 9,
 # the two TR updates 10) plus one add per dot product c_p . v on the 12 edge links (5 dot products).
 K4_FLOPS_PER_NODE_SPECIES = 63 + 57 + 19 * 36 + 12 * 5
+STAGE_STEPS = 20  # steps of the instrumented pass that gives the per-stage times
 
 WORKLOAD_TEXT = {
     "well256": "D3Q19 256^3 periodic, 1 species, sigma 6, packing 0.3 (+-1% noise, seed 1202), Gaussian well "
@@ -621,7 +622,8 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
     if sampler:
         sampler.start()
         time.sleep(0.5)
-    sim.set_stage_timing(True)
+    # the timed region holds the steps alone; the per-stage event times come from a second, shorter
+    # pass afterwards (the events between kernels stay out of the headline number)
     l0 = sim.launch_count()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -641,9 +643,13 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
         sampler.mark("t1")
     ms = e0.elapsed_time(e1)
     launches = sim.launch_count() - l0
+    clocks = sampler.stop() if sampler else None
+    stage_steps = min(steps, STAGE_STEPS)
+    sim.set_stage_timing(True)
+    sim.step(stage_steps)
+    torch.cuda.synchronize()
     stages = sim.stage_times()
     sim.set_stage_timing(False)
-    clocks = sampler.stop() if sampler else None
     state = "finite"
     try:
         _, _, umax = sim.totals()
@@ -671,11 +677,11 @@ def measure(args, wname, prec, steps, warmup, dist, world, local, peaks, peaks_k
                       "l2": "inputs larger than L2: population buffers %.2f GB each" % (N * M * 2 * QPOP * sb / 1e9),
                       "parallelism": "replicas only (one independent lattice per GPU)" if world > 1 else "1 GPU"},
            "roofline": roof,
-           "stage_ms_per_step": {k: v[0] / steps for k, v in stages.items()},
+           "stage_ms_per_step": {k: v[0] / stage_steps for k, v in stages.items()},
            "population_gbs_whole_step": step_bytes / (ms_step * 1e-3) / 1e9,
            "population_gbs_whole_step_frac": step_bytes / (ms_step * 1e-3) / 1e9 / hbm,
            "kernels": res_kernels,
-           "step_roofline": step_roofline(w, prec, N, M, sb, ms_step, {k: v[0] / steps for k, v in stages.items()},
+           "step_roofline": step_roofline(w, prec, N, M, sb, ms_step, {k: v[0] / stage_steps for k, v in stages.items()},
                                           res_kernels, hbm,
                                           (sms * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0))
                                            * 1e6 / 1e12) if prec != "fp64" else FP64_NOMINAL_TFLOPS,
