@@ -43,6 +43,10 @@ struct PairShell {
 
 }  // namespace
 
+#ifndef LBE_SHELL_STREAMS
+#define LBE_SHELL_STREAMS 2
+#endif
+
 struct lbe_ctx {
     lbe_config cfg{};
     Prec prec = Prec::F32;
@@ -108,6 +112,10 @@ struct lbe_ctx {
     long long launches = 0;
     long long steps_since_check = 0;
     std::string last_error;
+
+    // second stream of the shell stage: the pair launches of odd species run there (created on first use)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 
     // stage timing
     bool timing = false;
@@ -200,12 +208,13 @@ cudaEvent_t pool_event(lbe_ctx *c) {
     return e;
 }
 
-// Brackets one kernel launch of a stage with events when timing is on.
+// Brackets the kernel launches of a stage (count of them) with events when timing is on.
 struct StageTimer {
     lbe_ctx *c;
     int stage;
+    int count;
     cudaEvent_t a = nullptr, b = nullptr;
-    StageTimer(lbe_ctx *c_, int st) : c(c_), stage(st) {
+    StageTimer(lbe_ctx *c_, int st, int n = 1) : c(c_), stage(st), count(n) {
         if (c->timing) {
             a = pool_event(c);
             b = pool_event(c);
@@ -216,7 +225,7 @@ struct StageTimer {
         if (c->timing && a && b) {
             cudaEventRecord(b, c->stream);
             c->ev_pending[stage].push_back({a, b});
-            c->stage_launches[stage] += 1;
+            c->stage_launches[stage] += count;
         }
     }
 };
@@ -738,7 +747,21 @@ lbe_status force_stage_core(lbe_ctx *c, const void *pop, void *Pbase, void *xiba
         L.err = (int *)c->err.p;
         LAUNCH(launch_contact_tma(f64, L, c->stream), "contact kernel");
     }
+    // Two or more species: the pairs of odd species a run on a second stream beside those of even a. Each
+    // species' C still takes its pairs in order on one stream, and the launches of the two streams fill
+    // each other's last partial wave (one thread block per SM at a time).
+    const bool two = LBE_SHELL_STREAMS == 2 && c->M >= 2;
+    if (two && !c->side) {
+        CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "create the shell stage's second stream");
+        CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "create fork event");
+        CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "create join event");
+    }
     std::vector<int> first(c->M, 1);
+    StageTimer shell_timer(c, LBE_STAGE_SHELL, (int)c->pairs.size());
+    if (two) {
+        CK(cudaEventRecord(c->ev_fork, c->stream), "record fork");
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork the shell stage");
+    }
     for (size_t q = 0; q < c->pairs.size(); ++q) {
         const PairShell &ps = c->pairs[q];
         ShellLaunch L{};
@@ -753,8 +776,11 @@ lbe_status force_stage_core(lbe_ctx *c, const void *pop, void *Pbase, void *xiba
         L.accumulate = first[ps.a] ? 0 : 1;
         L.err = (int *)c->err.p;
         first[ps.a] = 0;
-        StageTimer t(c, LBE_STAGE_SHELL);
-        LAUNCH(launch_shell_force(f64, ps.S, L, c->stream), "shell force kernel");
+        LAUNCH(launch_shell_force(f64, ps.S, L, two && (ps.a & 1) ? c->side : c->stream), "shell force kernel");
+    }
+    if (two) {
+        CK(cudaEventRecord(c->ev_join, c->side), "record join");
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join the shell stage");
     }
     for (int a = 0; a < c->M; ++a)
         if (first[a]) CK(cudaMemsetAsync((char *)c->C.p + rb * 3 * a * c->g.N, 0, rb * 3 * c->g.N, c->stream),
@@ -971,6 +997,12 @@ void lbe_destroy(lbe_ctx *c) {
     fold_stage_times(c);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     c->ev_pool.clear();
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->ev_fork);
+        cudaEventDestroy(c->ev_join);
+    }
     Buf *all[] = {&c->pop[0], &c->pop[1], &c->solid, &c->mask, &c->V, &c->phi, &c->amp, &c->F,
                   &c->npad, &c->gab, &c->gnpad, &c->C, &c->flux_buf, &c->flux_acc,
                   &c->flux_last, &c->err, &c->scratch64, &c->partial, &c->red_out, &c->res_rec,
