@@ -141,7 +141,10 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     for (int s = 0; s < nsuper; ++s) {
         const int j0 = s * TZ;
         for (int j = j0; j < j0 + NK; ++j)
-            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+                mbar_drain(bars, Tl::R, j, min(j0 + Tl::R, nplanes));
+                return;
+            }
         if (active) {
             T nb[TZ], gr[TZ], oln[TZ], olg[TZ];
             long long idx[TZ];
@@ -276,7 +279,10 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     for (int s = 0; s < nsuper; ++s) {
         const int j0 = s * TZ;
         for (int j = j0; j < j0 + NK; ++j)
-            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+                mbar_drain(bars, Tl::R, j, min(j0 + Tl::R, nplanes));
+                return;
+            }
         if (active) {
             float nb[TZ], gr[TZ], oln[TZ], olg[TZ];
             long long idx[TZ];

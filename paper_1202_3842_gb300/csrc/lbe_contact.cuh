@@ -106,7 +106,10 @@ __global__ void __launch_bounds__(256)
     if (leader)
         for (int j = 0; j < 2 * RB + 1 && j < nplanes; ++j) issue(j);
     for (int j = 0; j < 2 * RB; ++j)
-        if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+        if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+            mbar_drain(bars, Tl::R, j, min(2 * RB + 1, nplanes));
+            return;
+        }
 
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < g.nx) && (y < g.ny);
@@ -118,7 +121,10 @@ __global__ void __launch_bounds__(256)
             issue(iz + 2 * RB + 1);
         }
         const int jn = iz + 2 * RB;
-        if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) return;
+        if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) {
+            mbar_drain(bars, Tl::R, jn, min(iz + 2 * RB + 2, nplanes));
+            return;
+        }
         if (active) {
             T xi2 = 0, xi3 = 0, nloc[M];
             const T *sb[2 * RB + 1];

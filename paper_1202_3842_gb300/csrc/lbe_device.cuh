@@ -211,6 +211,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return false;
 }
 
+// After a wait gave up: wait again, with a bound, for the copies this CTA issued into planes [j, jend)
+// of its ring of R slots (plane j in slot j % R, phase j / R), so that none of them lands in shared
+// memory after the CTA has exited.  Each plane gets at most 2^20 polls or 0.1 s on %globaltimer; the
+// error bit is already set.  Kept out of line: it runs only on the failure path.
+constexpr long long DRAIN_POLLS = 1ll << 20;
+constexpr unsigned long long DRAIN_NS = 100000000ull;
+static __device__ __noinline__ void mbar_drain(uint64_t *bars, int R, int j, int jend) {
+    for (; j < jend; ++j) {
+        uint64_t *b = bars + (j % R);
+        const uint32_t parity = (uint32_t)(j / R) & 1u;
+        const unsigned long long t0 = globaltimer_ns();
+        for (long long it = 0; it < DRAIN_POLLS; ++it) {
+            if (mbar_try_wait(b, parity)) break;
+            if ((it & 255) == 255 && globaltimer_ns() - t0 > DRAIN_NS) break;
+        }
+    }
+}
+
 __device__ __forceinline__ void mbar_inval(uint64_t *bar) {
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }

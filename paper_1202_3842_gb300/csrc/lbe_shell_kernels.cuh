@@ -118,7 +118,10 @@ __global__ void __launch_bounds__(32 * ShellTile<T, S>::TY)
         for (int j = 0; j < 2 * S + 1 && j < nplanes; ++j) issue(j);
     }
     for (int j = 0; j < 2 * S; ++j)
-        if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+        if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+            mbar_drain(bars, Tl::R, j, min(2 * S + 1, nplanes));
+            return;
+        }
 
     const int x = x0 + tx, y = y0 + ty;
     const bool active = (x < g.nx) && (y < g.ny);
@@ -131,7 +134,10 @@ __global__ void __launch_bounds__(32 * ShellTile<T, S>::TY)
             issue(iz + 2 * S + 1);
         }
         const int jn = iz + 2 * S;
-        if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) return;
+        if (!mbar_wait_bounded(&bars[jn % Tl::R], (jn / Tl::R) & 1, err)) {
+            mbar_drain(bars, Tl::R, jn, min(iz + 2 * S + 2, nplanes));
+            return;
+        }
         if (active) {
             const T *sb[2 * S + 1];
 #pragma unroll
@@ -310,7 +316,10 @@ __global__ void __launch_bounds__(32 * TYB, 1)
     for (int s = 0; s < nsuper; ++s) {
         const int j0 = s * TZ;
         for (int j = j0; j < j0 + NK; ++j)
-            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+                mbar_drain(bars, Tl::R, j, min(j0 + Tl::R, nplanes));
+                return;
+            }
         if (active) {
             // the epilogue's global loads are issued before the shell sum so their latency hides behind it
             float na[TZ], gr[TZ], old[TZ][3];
@@ -518,7 +527,10 @@ __global__ void __launch_bounds__(32 * TYT, 1)
     for (int s = 0; s < nsuper; ++s) {
         const int j0 = s * TZ;
         for (int j = j0; j < j0 + NK; ++j)
-            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) return;
+            if (!mbar_wait_bounded(&bars[j % Tl::R], (j / Tl::R) & 1, err)) {
+                mbar_drain(bars, Tl::R, j, min(j0 + Tl::R, nplanes));
+                return;
+            }
         if (x < g.nx && yb < g.ny) {
             // the epilogue's global loads are issued before the shell sum so their latency hides behind it
             float pre[2][TZ], gr[2][TZ], old[2][TZ][3];
