@@ -758,9 +758,22 @@ lbe_status force_stage_core(lbe_ctx *c, const void *pop, void *Pbase, void *xiba
     }
     std::vector<int> first(c->M, 1);
     StageTimer shell_timer(c, LBE_STAGE_SHELL, (int)c->pairs.size());
+    // joins the second stream back on an early return too, so that later work on the main stream
+    // never runs beside a pair launch already queued there
+    struct SideJoin {
+        lbe_ctx *c;
+        bool pending;
+        ~SideJoin() {
+            if (pending) {
+                cudaEventRecord(c->ev_join, c->side);
+                cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+            }
+        }
+    } side_join{c, false};
     if (two) {
         CK(cudaEventRecord(c->ev_fork, c->stream), "record fork");
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "fork the shell stage");
+        side_join.pending = true;
     }
     for (size_t q = 0; q < c->pairs.size(); ++q) {
         const PairShell &ps = c->pairs[q];
@@ -779,6 +792,7 @@ lbe_status force_stage_core(lbe_ctx *c, const void *pop, void *Pbase, void *xiba
         LAUNCH(launch_shell_force(f64, ps.S, L, two && (ps.a & 1) ? c->side : c->stream), "shell force kernel");
     }
     if (two) {
+        side_join.pending = false;
         CK(cudaEventRecord(c->ev_join, c->side), "record join");
         CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0), "join the shell stage");
     }
